@@ -1,0 +1,179 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+* Exact (untruncated) moves reproduce brute-force finite-lattice density
+  matrices, in both modes and all four directions (Sec. II: a move absorbs a
+  column; with chi large no projector truncates).
+* The sequential ket-then-bra absorption with split isometries equals the
+  double-layer absorption with the composed 4-index isometry (Sec. IV: the
+  sequential order only re-brackets v = v^1 v^2).
+* D = 1 product states: <S.S> factorises exactly, in both modes.
+* The Ising-norm PEPS reproduces Onsager's free energy and nearest-neighbour
+  correlation and Yang's magnetisation.
+* Four quarter turns of a site are the identity.
+"""
+import numpy as np
+import pytest
+
+from oracle import ctm_oracle as O
+from oracle import onsager as ON
+from paper_2306_08212_gb300 import inputs as I
+from tests import brute
+
+
+HUGE = 10 ** 6  # a bond dimension that never truncates
+
+
+def _iso(rng, m, n):
+    q, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    return q
+
+
+def test_rotation_four_quarter_turns_is_identity():
+    A, _ = I.random_sites(2, 3, 5)
+    assert np.array_equal(O.rotate_site(A, 4), A)
+    # one quarter turn moves the up leg to the left slot
+    R = O.rotate_site(A, 1)
+    assert np.array_equal(R[:, 1, 2, 0, 1], A[:, 2, 0, 1, 1])
+
+
+def test_sequential_absorption_equals_double_layer_with_composed_isometries():
+    rng = np.random.default_rng(3)
+    d, D, chi, chip = 2, 3, 5, 4
+    T = rng.standard_normal((chi, D, D, chi))
+    A = rng.standard_normal((d, D, D, D, D))
+    S = O.edge_site_T1(A)
+    vp1 = _iso(rng, chi * D, chip).reshape(chi, D, chip)
+    vp2 = _iso(rng, chip * D, chi).reshape(chip, D, chi)
+    vn1 = _iso(rng, chi * D, chip).reshape(chi, D, chip)
+    vn2 = _iso(rng, chip * D, chi).reshape(chip, D, chi)
+    seq = O.absorb_edge_seq(T, S, vp1, vp2, vn1, vn2)
+    dbl = O.absorb_edge_double(T, S, O.compose(vp1, vp2), O.compose(vn1, vn2))
+    assert seq.shape == (chi, D, D, chi)
+    np.testing.assert_allclose(seq, dbl, rtol=0, atol=1e-13 * np.abs(dbl).max())
+
+
+def test_sequential_absorption_checks_every_leg():
+    """A planted transposition (prev <-> next projector) must break the equality."""
+    rng = np.random.default_rng(4)
+    d, D, chi = 2, 2, 3
+    T = rng.standard_normal((chi, D, D, chi))
+    A = rng.standard_normal((d, D, D, D, D))
+    S = O.edge_site_T1(A)
+    vs = [_iso(rng, chi * D, chi).reshape(chi, D, chi) for _ in range(4)]
+    good = O.absorb_edge_double(T, S, O.compose(vs[0], vs[1]), O.compose(vs[2], vs[3]))
+    bad = O.absorb_edge_seq(T, S, vs[2], vs[1], vs[0], vs[3])
+    assert np.abs(good - bad).max() > 1e-3
+
+
+def _env_fold(A, B):
+    env = O.fold_init(A, B)
+    return {k: O._normalize(v) for k, v in env.items()}
+
+
+@pytest.mark.parametrize("mode", ["standard", "reduced_sequential"])
+def test_fold_and_exact_moves_match_brute_force(mode):
+    d, D = 2, 2
+    A, B = I.random_sites(d, D, 11)
+    env = _env_fold(A, B)
+    # no move: each 1x2 window sits in a 3 x 4 patch
+    # bond 0: a at (1,1); bond 1: b at (1,1)
+    for bond, par in ((0, 0), (1, 1)):
+        ref = brute.finite_rdm(A, B, 3, 4, ((1, 1), (1, 2)), a_parity=par)
+        rho = O.bond_rdm(env, A, B, 0, "a" if bond == 0 else "b")
+        np.testing.assert_allclose(rho / np.trace(rho), ref / np.trace(ref), atol=1e-13)
+    # one exact left move adds two columns on the left, one exact right move
+    # two on the right: a 3 x 8 patch with the pair at columns 3, 4
+    O.move(env, "left", A, B, HUGE, HUGE, mode)
+    O.move(env, "right", A, B, HUGE, HUGE, mode)
+    for bond, par in ((0, 0), (1, 1)):
+        ref = brute.finite_rdm(A, B, 3, 8, ((1, 3), (1, 4)), a_parity=par)
+        rho = O.bond_rdm(env, A, B, 0, "a" if bond == 0 else "b")
+        np.testing.assert_allclose(rho / np.trace(rho), ref / np.trace(ref), atol=1e-12)
+
+
+@pytest.mark.parametrize("mode", ["standard", "reduced_sequential"])
+def test_exact_vertical_moves_match_brute_force(mode):
+    d, D = 2, 2
+    A, B = I.random_sites(d, D, 12)
+    env = _env_fold(A, B)
+    O.move(env, "up", A, B, HUGE, HUGE, mode)
+    O.move(env, "down", A, B, HUGE, HUGE, mode)
+    # in the frame turned one quarter counter-clockwise the vertical pair is
+    # horizontal and the up/down moves are left/right moves
+    Ar, Br = O.rotate_site(A, 1), O.rotate_site(B, 1)
+    for x, par in (("a", 0), ("b", 1)):
+        ref = brute.finite_rdm(Ar, Br, 3, 8, ((1, 3), (1, 4)), a_parity=par)
+        rho = O.bond_rdm(env, A, B, 1, x)
+        np.testing.assert_allclose(rho / np.trace(rho), ref / np.trace(ref), atol=1e-12)
+
+
+@pytest.mark.parametrize("mode", ["standard", "reduced_sequential"])
+def test_product_state_factorises(mode):
+    pa = np.array([0.8, 0.6])
+    pb = np.array([0.28, -0.96])
+    A, B = I.product_sites(pa, pb)
+    env = O.init_env(A, B, 4)
+    O.converge(env, A, B, 4, 4, mode, max_iter=3)
+    sx = np.array([[0, 1], [1, 0]]) / 2
+    sz = np.array([[1, 0], [0, -1]]) / 2
+    ma = np.array([pa @ sx @ pa, pa @ sz @ pa])
+    mb = np.array([pb @ sx @ pb, pb @ sz @ pb])
+    exact = float(ma @ mb)  # <Sy> vanishes for real spinors
+    H = O.heisenberg_bond()
+    for bond in range(4):
+        assert abs(O.expect_bond(env, A, B, bond, H) - exact) < 1e-14
+
+
+def test_neel_product_state_energy():
+    A, B = I.neel_sites(1, eps=0.0)
+    env = O.init_env(A, B, 4)
+    O.converge(env, A, B, 4, 4, "reduced_sequential", max_iter=2)
+    for bond in range(4):
+        assert abs(O.expect_bond(env, A, B, bond, O.heisenberg_bond()) + 0.25) < 1e-15
+
+
+def test_onsager_closed_forms_agree_with_each_other():
+    for beta in (0.40, 0.44, 0.48):
+        assert abs(ON.lnz_double_integral(beta) - ON.lnz_single_integral(beta)) < 1e-12
+        # <s s'> = (1/2) d(ln Z / N)/d beta: two bonds per site
+        h = 1e-5
+        der = (ON.lnz_single_integral(beta + h) - ON.lnz_single_integral(beta - h)) / (2 * h)
+        assert abs(0.5 * der - ON.nn_correlation(beta)) < 1e-6
+
+
+def test_onsager_golden_table():
+    rows = np.loadtxt("tests/golden/onsager.txt", comments="#")
+    for beta, lnz, nn, m in rows:
+        assert abs(ON.lnz_single_integral(beta) - lnz) < 1e-12
+        assert abs(ON.nn_correlation(beta) - nn) < 1e-12
+        assert abs(ON.magnetization(beta) - m) < 1e-12
+
+
+def _ising_run(beta, chi, mode, plus_boundary, iters):
+    A, W = I.ising_peps(beta)
+    bnd = np.outer(W[0], W[0]) if plus_boundary else None
+    env = O.init_env(A, A, chi, bnd)
+    O.converge(env, A, A, chi, chi, mode, max_iter=iters, tol=1e-13)
+    sz = np.diag([1.0, -1.0])
+    zz = O.expect_bond(env, A, A, 0, np.kron(sz, sz))
+    m = O.expect_bond(env, A, A, 0, np.kron(sz, np.eye(2)))
+    lk = O.log_kappa_sites(env, A, A)
+    return lk, zz, m
+
+
+@pytest.mark.parametrize("mode", ["standard", "reduced_sequential"])
+def test_ising_high_temperature_matches_onsager(mode):
+    beta = 0.40
+    lk, zz, m = _ising_run(beta, 16, mode, False, 60)
+    assert abs(lk - ON.lnz_single_integral(beta)) < 2e-6
+    assert abs(zz - ON.nn_correlation(beta)) < 2e-4
+    assert abs(m) < 1e-10
+
+
+@pytest.mark.parametrize("mode", ["standard", "reduced_sequential"])
+def test_ising_ordered_phase_matches_onsager_and_yang(mode):
+    beta = 0.48
+    lk, zz, m = _ising_run(beta, 16, mode, True, 60)
+    assert abs(lk - ON.lnz_single_integral(beta)) < 2e-6
+    assert abs(zz - ON.nn_correlation(beta)) < 2e-4
+    assert abs(m - ON.magnetization(beta)) < 2e-4
