@@ -1,0 +1,141 @@
+/*
+ * ctm.h -- C ABI of libctm, a GB300 (sm_103a) implementation of the
+ * corner-transfer-matrix (CTM) move for a square-lattice iPEPS with a 2-site
+ * {A, B} unit cell, in the standard form and in the reduced-environment,
+ * sequential-order form of Lan & Evenbly, "Reduced Contraction Costs of
+ * Corner-Transfer Methods for PEPS".
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Site tensors A, B are real, row-major [d][D][D][D][D] with legs (p, u, l, d, r)
+ * (Sec. II: physical dimension d, virtual dimension D).  Site (i, j) of the
+ * lattice holds A when i + j is even.
+ *
+ * The environment (Sec. II, Fig. 1d) is stored as 16 tensors (kind, k, x):
+ * kind 0 = corner C, 1 = edge T; k = 1 (left / top-left), 2 (top / top-right),
+ * 3 (right / bottom-right), 4 (bottom / bottom-left); x = 0 for sublattice a,
+ * 1 for b (the site the tensor is adjacent to).  Legs run clockwise around the
+ * boundary: corners are [prev][next] (C1[down][right], C2[left][down],
+ * C3[up][left], C4[right][up]); edges are [prev][ket][bra][next]
+ * (T1[down][k][b][up], T2[left][k][b][right], T3[up][k][b][down],
+ * T4[right][k][b][left]).
+ *
+ * Moves: dir 0 = left, 1 = up, 2 = right, 3 = down.  A move absorbs two
+ * columns (Sec. II, Fig. 2a); the up, right and down moves are the left move
+ * of the lattice turned counter-clockwise by 1, 2, 3 quarter turns.
+ *
+ * Errors: every int-returning call returns CTM_OK (0) or a negative code and
+ * never aborts the process; ctm_last_error() describes the last failure of a
+ * context.  All device work is issued on the stream given to ctm_init_env.
+ * Calls on one context must not overlap (the context is not thread-safe).
+ */
+#ifndef CTM_H
+#define CTM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ctm_ctx ctm_ctx;
+
+enum {
+  CTM_OK = 0,
+  CTM_ERR_ARG = -1,         /* bad argument (size, enum, null pointer) */
+  CTM_ERR_OOM = -2,         /* device or host allocation failed */
+  CTM_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  CTM_ERR_NAN = -4,         /* a NaN/Inf or zero-norm tensor was produced */
+  CTM_ERR_NOCONV = -5,      /* iteration / Jacobi sweep cap reached */
+  CTM_ERR_UNSUPPORTED = -6  /* combination not built in this library */
+};
+
+enum { CTM_LEFT = 0, CTM_UP = 1, CTM_RIGHT = 2, CTM_DOWN = 3 };
+enum { CTM_STANDARD = 0, CTM_REDUCED_SEQUENTIAL = 1 };
+/* Arithmetic of the absorption / renormalisation contractions.  Projector
+ * factorisations, normalisation, spectra and observables are FP64 always. */
+enum { CTM_FP64 = 0, CTM_TF32 = 1, CTM_BF16 = 2 };
+
+/*
+ * Create a context, copy A and B (host or device pointers, detected with
+ * cudaPointerGetAttributes; the caller keeps ownership), and build the
+ * initial environment: every tensor is a site whose outward legs are closed by
+ * `boundary` (D x D row-major, ket x bra; NULL = identity, i.e. each outward
+ * ket leg traced with its bra partner), giving bond dimension D^2; standard
+ * moves (Sec. II) then grow every bond to chi (the reduced networks of
+ * Sec. III-IV cannot raise a bond above the current one).
+ * chi_prime is the intermediate dimension chi' of the split isometries
+ * (Sec. IV; the paper uses chi' = chi); pass 0 for chi.
+ * stream: a cudaStream_t (NULL = the legacy default stream).
+ * The context owns all device memory it allocates; free it with ctm_free.
+ */
+int ctm_init_env(ctm_ctx** out, const double* A, const double* B, int d, int D,
+                 int chi, int chi_prime, int precision, const double* boundary,
+                 void* stream);
+
+/*
+ * One CTM move in direction dir (Sec. II; mode CTM_STANDARD uses the 8-tensor
+ * half-network projector of Fig. 2c, mode CTM_REDUCED_SEQUENTIAL the reduced
+ * network of Fig. 3c / Fig. 8 with split isometries and the ket-then-bra
+ * absorption of Fig. 4).  Every new tensor is scaled to unit Frobenius norm.
+ * Returns CTM_ERR_NAN if a tensor became non-finite or zero.
+ */
+int ctm_move(ctm_ctx* ctx, int dir, int mode);
+
+/*
+ * Repeat iterations of (left, up, right, down) moves until the 8 corner
+ * spectra (each scaled to sum s^2 = 1) change by less than tol in 2-norm
+ * (maximum over corners), or max_iter iterations ran (Sec. II: N_CTM ~ 10-30).
+ * Writes the iterations done and the last change; returns CTM_ERR_NOCONV when
+ * max_iter was reached without convergence.
+ */
+int ctm_converge(ctm_ctx* ctx, int mode, int max_iter, double tol,
+                 int* iters_done, double* last_delta);
+
+/*
+ * <op> on one nearest-neighbour bond from the 2-site reduced density matrix of
+ * the environment: bond 0 = a left of b, 1 = b left of a, 2 = a above b,
+ * 3 = b above a.  op is host, row-major (d*d) x (d*d) with rows and columns
+ * ordered (first site, second site).  The result is written to *value (host).
+ */
+int ctm_expect_bond(ctm_ctx* ctx, int bond, const double* op, double* value);
+
+/*
+ * Singular values of corner `corner` (0..7 = C1a, C1b, C2a, C2b, C3a, C3b,
+ * C4a, C4b), descending and scaled to sum s^2 = 1.  s is a host buffer of at
+ * least chi entries; *len receives the count written.
+ */
+int ctm_corner_spectrum(ctm_ctx* ctx, int corner, double* s, int* len);
+
+/*
+ * Per-site log norm ln kappa = (1/4) ln[Z22 Z00 / (Z20 Z02)] from the 2x2
+ * window with top-left site a, where Zhw closes the environment around an
+ * h x w block of sites (corner and edge normalisations cancel).  For the
+ * Ising-norm PEPS this is ln Z / N.
+ */
+int ctm_log_kappa(ctm_ctx* ctx, double* value);
+
+/*
+ * Copy environment tensor (kind, k, x) to the host buffer `out` (may be NULL
+ * to query) and its 2 (corner) or 4 (edge) dims to dims[0..3].
+ */
+int ctm_get_tensor(ctm_ctx* ctx, int kind, int k, int x, double* out, int* dims);
+
+/*
+ * Overwrite environment tensor (kind, k, x) from a host buffer with the given
+ * dims (2 for a corner, 4 for an edge; bond dims at most chi, ket/bra dims D).
+ */
+int ctm_set_tensor(ctm_ctx* ctx, int kind, int k, int x, const double* in,
+                   const int* dims);
+
+/* Number of kernels this library launched on the context so far. */
+long long ctm_kernel_launches(ctm_ctx* ctx);
+
+/* Message of the last failure on ctx ("" if none); valid until the next call. */
+const char* ctm_last_error(ctm_ctx* ctx);
+
+/* Release every device and host resource of ctx (NULL is allowed). */
+void ctm_free(ctm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTM_H */

@@ -364,7 +364,7 @@ def grow(env, A, B, chi, max_iter=16):
     """
     for _ in range(max_iter):
         before = bond_dims(env)
-        if all(max(s[0], s[-1]) >= chi for s in before.values()):
+        if all(min(s[0], s[-1]) >= chi for s in before.values()):
             break
         for d in MOVE_ORDER:
             move(env, d, A, B, chi, chi, "standard")

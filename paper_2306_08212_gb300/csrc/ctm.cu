@@ -1,0 +1,1091 @@
+// Host orchestrator and C ABI of libctm: environment storage, the CTM moves in
+// the standard and the reduced-sequential form, projector factorisations,
+// observables.  Every arithmetic step runs in this library's CUDA kernels; the
+// host only sequences launches and reads back scalars.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/ctm.h"
+#include "ctm_internal.h"
+#include "tc_gemm.h"
+
+using namespace ctm;
+
+namespace {
+
+struct CtmError {
+  int code;
+  std::string msg;
+};
+
+[[noreturn]] void fail(int code, const std::string& msg) { throw CtmError{code, msg}; }
+
+void ck(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) fail(CTM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+constexpr int kExactSvdMax = 512;  // exact one-sided Jacobi below this size
+constexpr int kOversample = 16;    // randomized range finder: extra columns
+constexpr int kPowerIters = 2;     // randomized range finder: subspace iterations
+constexpr int kMaxSweeps = 60;
+
+}  // namespace
+
+struct ctm_ctx {
+  cudaStream_t stream = nullptr;
+  int d = 0, D = 0, chi = 0, chip = 0, precision = CTM_FP64;
+  double* site[4][2] = {};  // rotated copies rot^r(A), rot^r(B): [r][x]
+  double* dbl[4][2] = {};   // double-layer tensors a (fused legs), built on first use
+  double* bnd = nullptr;    // boundary matrix (D x D)
+  Ten env[2][4][2];         // [kind][k-1][x]: the current tensors
+  double* buf[2][4][2][2] = {};  // two buffers per tensor
+  int cur[2][4][2] = {};
+  DevFlags* flags = nullptr;
+  double* norm_scratch = nullptr;
+  long long launches = 0;
+  unsigned long long seed = 0x5eed;
+  std::string err;
+  std::vector<void*> owned;  // long-lived device allocations
+  TcGemm* tc = nullptr;      // tensor-core GEMM state (mixed precision)
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Device memory
+// ---------------------------------------------------------------------------
+double* dalloc(ctm_ctx* c, long long n) {
+  void* p = nullptr;
+  if (n <= 0) n = 1;
+  cudaError_t e = cudaMallocAsync(&p, (size_t)n * sizeof(double), c->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(CTM_ERR_OOM, "device allocation of " + std::to_string(n * 8) + " bytes failed");
+  }
+  return (double*)p;
+}
+
+void dfree(ctm_ctx* c, void* p) {
+  if (p) cudaFreeAsync(p, c->stream);
+}
+
+double* owned_alloc(ctm_ctx* c, long long n) {
+  void* p = nullptr;
+  if (n <= 0) n = 1;
+  if (cudaMalloc(&p, (size_t)n * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    fail(CTM_ERR_OOM, "device allocation failed");
+  }
+  c->owned.push_back(p);
+  return (double*)p;
+}
+
+// A temporary tensor freed (stream-ordered) when it leaves scope.
+struct Tmp {
+  ctm_ctx* c = nullptr;
+  Ten t;
+  Tmp() = default;
+  Tmp(ctm_ctx* ctx, std::initializer_list<int> dims) : c(ctx) {
+    t.nd = 0;
+    for (int v : dims) t.dims[t.nd++] = v;
+    t.p = dalloc(c, t.size());
+  }
+  Tmp(ctm_ctx* ctx, const int* dims, int nd) : c(ctx) {
+    t.nd = nd;
+    for (int i = 0; i < nd; ++i) t.dims[i] = dims[i];
+    t.p = dalloc(c, t.size());
+  }
+  Tmp(const Tmp&) = delete;
+  Tmp& operator=(const Tmp&) = delete;
+  Tmp(Tmp&& o) noexcept : c(o.c), t(o.t) { o.t.p = nullptr; }
+  Tmp& operator=(Tmp&& o) noexcept {
+    if (this != &o) {
+      release();
+      c = o.c;
+      t = o.t;
+      o.t.p = nullptr;
+    }
+    return *this;
+  }
+  ~Tmp() { release(); }
+  void release() {
+    if (t.p && c) dfree(c, t.p);
+    t.p = nullptr;
+  }
+  operator const Ten&() const { return t; }
+};
+
+Ten view(const Ten& t, std::initializer_list<int> dims) {
+  Ten v;
+  v.p = t.p;
+  v.nd = 0;
+  long long s = 1;
+  for (int x : dims) {
+    v.dims[v.nd++] = x;
+    s *= x;
+  }
+  if (s != t.size()) fail(CTM_ERR_ARG, "internal: reshape size mismatch");
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Pairwise contraction "labelsA,labelsB->labelsOut" on FP64 tensors
+// ---------------------------------------------------------------------------
+struct Spec {
+  std::string a, b, o;
+};
+
+Spec parse(const char* spec) {
+  Spec s;
+  const char* comma = std::strchr(spec, ',');
+  const char* arrow = std::strstr(spec, "->");
+  if (!comma || !arrow || arrow < comma) fail(CTM_ERR_ARG, std::string("internal: bad spec ") + spec);
+  s.a.assign(spec, comma);
+  s.b.assign(comma + 1, arrow);
+  s.o.assign(arrow + 2);
+  return s;
+}
+
+void strides_of(const Ten& t, long long* st) {
+  long long s = 1;
+  for (int i = t.nd - 1; i >= 0; --i) {
+    st[i] = s;
+    s *= t.dims[i];
+  }
+}
+
+struct Plan {
+  long long M = 1, N = 1, K = 1;
+  LegMap Am, Ak, Bk, Bn, Cm, Cn;
+  int out_dims[kMaxLegs];
+  int out_nd = 0;
+};
+
+void push(LegMap& m, int dim, long long stride) {
+  if (m.n >= kMaxLegs) fail(CTM_ERR_ARG, "internal: too many legs");
+  m.dim[m.n] = dim;
+  m.stride[m.n] = stride;
+  ++m.n;
+}
+
+// Merge neighbouring sub-legs that are contiguous in both maps (fewer div/mods).
+void merge_pair(LegMap& x, LegMap& y) {
+  int w = 0;
+  for (int i = 0; i < x.n; ++i) {
+    if (w > 0 && x.stride[w - 1] == (long long)x.dim[i] * x.stride[i] &&
+        y.stride[w - 1] == (long long)y.dim[i] * y.stride[i]) {
+      x.dim[w - 1] *= x.dim[i];
+      x.stride[w - 1] = x.stride[i];
+      y.dim[w - 1] = x.dim[w - 1];
+      y.stride[w - 1] = y.stride[i];
+    } else {
+      x.dim[w] = x.dim[i];
+      x.stride[w] = x.stride[i];
+      y.dim[w] = y.dim[i];
+      y.stride[w] = y.stride[i];
+      ++w;
+    }
+  }
+  x.n = y.n = w;
+}
+
+Plan make_plan(const Spec& s, const Ten& A, const Ten& B) {
+  if ((int)s.a.size() != A.nd || (int)s.b.size() != B.nd)
+    fail(CTM_ERR_ARG, "internal: spec rank mismatch " + s.a + "," + s.b);
+  long long sa[kMaxLegs], sb[kMaxLegs];
+  strides_of(A, sa);
+  strides_of(B, sb);
+  auto dim_of = [&](char ch) -> int {
+    size_t i = s.a.find(ch);
+    if (i != std::string::npos) return A.dims[i];
+    i = s.b.find(ch);
+    if (i != std::string::npos) return B.dims[i];
+    fail(CTM_ERR_ARG, std::string("internal: unknown label ") + ch);
+  };
+  Plan p;
+  p.out_nd = (int)s.o.size();
+  long long so[kMaxLegs];
+  for (int i = 0; i < p.out_nd; ++i) p.out_dims[i] = dim_of(s.o[i]);
+  {
+    long long st = 1;
+    for (int i = p.out_nd - 1; i >= 0; --i) {
+      so[i] = st;
+      st *= p.out_dims[i];
+    }
+  }
+  for (int i = 0; i < p.out_nd; ++i) {
+    const char ch = s.o[i];
+    const size_t ia = s.a.find(ch), ib = s.b.find(ch);
+    if (ia != std::string::npos && ib != std::string::npos)
+      fail(CTM_ERR_ARG, "internal: batch labels are not supported");
+    if (ia != std::string::npos) {
+      push(p.Am, A.dims[ia], sa[ia]);
+      push(p.Cm, A.dims[ia], so[i]);
+      p.M *= A.dims[ia];
+    } else if (ib != std::string::npos) {
+      push(p.Bn, B.dims[ib], sb[ib]);
+      push(p.Cn, B.dims[ib], so[i]);
+      p.N *= B.dims[ib];
+    } else {
+      fail(CTM_ERR_ARG, "internal: output label not in inputs");
+    }
+  }
+  for (int i = 0; i < A.nd; ++i) {
+    const char ch = s.a[i];
+    if (s.o.find(ch) != std::string::npos) continue;
+    const size_t ib = s.b.find(ch);
+    if (ib == std::string::npos) fail(CTM_ERR_ARG, "internal: traces are not supported");
+    if (A.dims[i] != B.dims[ib])
+      fail(CTM_ERR_ARG, std::string("internal: dim mismatch on label ") + ch + " in " + s.a +
+                            "," + s.b);
+    push(p.Ak, A.dims[i], sa[i]);
+    push(p.Bk, B.dims[ib], sb[ib]);
+    p.K *= A.dims[i];
+  }
+  for (int i = 0; i < B.nd; ++i)
+    if (s.o.find(s.b[i]) == std::string::npos && s.a.find(s.b[i]) == std::string::npos)
+      fail(CTM_ERR_ARG, "internal: traces are not supported");
+  merge_pair(p.Am, p.Cm);
+  merge_pair(p.Bn, p.Cn);
+  merge_pair(p.Ak, p.Bk);
+  return p;
+}
+
+// C = A . B per the spec, FP64 always (factorisation-side and observables).
+Tmp ein64(ctm_ctx* c, const char* spec, const Ten& A, const Ten& B) {
+  Plan p = make_plan(parse(spec), A, B);
+  Tmp C(c, p.out_dims, p.out_nd);
+  ck(gemm_f64(c->stream, p.M, p.N, p.K, 1.0, A.p, p.Am, p.Ak, B.p, p.Bk, p.Bn, 0.0, C.t.p, p.Cm,
+              p.Cn),
+     spec);
+  ++c->launches;
+  return C;
+}
+
+// Absorption / renormalisation contraction in the context's precision.
+Tmp ein(ctm_ctx* c, const char* spec, const Ten& A, const Ten& B) {
+  if (c->precision == CTM_FP64) return ein64(c, spec, A, B);
+  Plan p = make_plan(parse(spec), A, B);
+  Tmp C(c, p.out_dims, p.out_nd);
+  int rc = tc_contract(c->tc, c->stream, c->precision, p.M, p.N, p.K, A.p, p.Am, p.Ak, B.p,
+                       p.Bk, p.Bn, C.t.p, p.Cm, p.Cn, &c->launches);
+  if (rc != 0) fail(CTM_ERR_CUDA, std::string("tensor-core contraction failed: ") + spec);
+  return C;
+}
+
+// ---------------------------------------------------------------------------
+// Factorisations (FP64)
+// ---------------------------------------------------------------------------
+void jacobi(ctm_ctx* c, double* X, int nrows, int ncols, double* V) {
+  int rc = jacobi_onesided(c->stream, X, nrows, ncols, V, c->flags, kMaxSweeps, &c->launches);
+  if (rc != 0) fail(CTM_ERR_CUDA, "Jacobi launch failed");
+}
+
+Tmp identity(ctm_ctx* c, int n) {
+  Tmp I(c, {n, n});
+  ck(fill_identity(c->stream, I.t.p, n), "identity");
+  ++c->launches;
+  return I;
+}
+
+// Orthonormal, sign-fixed, descending-ordered columns of X (col-major nrows x ncols)
+// after Jacobi: U (row-major nrows x k) = X[:, perm[:k]] / sigma.
+Tmp sorted_unit_columns(ctm_ctx* c, double* X, int nrows, int ncols, int k) {
+  Tmp sig(c, {ncols});
+  int* perm = (int*)dalloc(c, (ncols + 1) / 2 + 1);
+  ck(column_norms_sorted(c->stream, X, nrows, ncols, sig.t.p, perm), "column norms");
+  Tmp U(c, {nrows, k});
+  ck(gather_sorted_columns(c->stream, U.t.p, nrows, k, X, nullptr, sig.t.p, perm), "gather");
+  c->launches += 3;
+  dfree(c, perm);
+  return U;
+}
+
+// Leading k left singular vectors of the row-major matrix M (rows x cols):
+// U (row-major rows x k).  Exact one-sided Jacobi when the smaller side is at
+// most kExactSvdMax, else a randomized subspace iteration (Halko, Martinsson &
+// Tropp, SIAM Rev. 53, 217 (2011)) with a Jacobi SVD of the projected problem.
+Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k);
+
+// CTM_TRACE=1 prints every factorisation (shape, path, time, Jacobi sweeps of
+// the last launch) to stderr; it synchronises the stream around each call.
+bool trace_on() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = std::getenv("CTM_TRACE");
+    on = (e && *e && *e != '0') ? 1 : 0;
+  }
+  return on == 1;
+}
+
+Tmp left_svd(ctm_ctx* c, const double* M, int rows, int cols, int k) {
+  if (!trace_on()) return left_svd_impl(c, M, rows, cols, k);
+  ck(cudaStreamSynchronize(c->stream), "sync");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, c->stream);
+  Tmp U = left_svd_impl(c, M, rows, cols, k);
+  cudaEventRecord(e1, c->stream);
+  ck(cudaStreamSynchronize(c->stream), "sync");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  DevFlags h;
+  cudaMemcpy(&h, c->flags, sizeof h, cudaMemcpyDeviceToHost);
+  const char* path = k >= rows ? "identity" : (std::min(rows, cols) <= kExactSvdMax ? "exact" : "randomized");
+  std::fprintf(stderr, "[ctm] svd %dx%d k=%d %s %.3f ms sweeps(last)=%d err=%d noconv=%d\n", rows,
+               cols, k, path, ms, h.sweeps, h.error, h.noconv);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return U;
+}
+
+Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k) {
+  if (k >= rows) return identity(c, rows);
+  if (k > std::min(rows, cols)) fail(CTM_ERR_ARG, "truncation rank exceeds the matrix rank bound");
+  if (std::min(rows, cols) <= kExactSvdMax) {
+    if (cols <= rows) {
+      // X = M column-major (transpose copy), Jacobi on its cols columns
+      Tmp X(c, {cols, rows});
+      LegMap m;
+      push(m, cols, 1);
+      push(m, rows, cols);
+      ck(permute_f64(c->stream, X.t.p, M, m), "transpose");
+      ++c->launches;
+      jacobi(c, X.t.p, rows, cols, nullptr);
+      return sorted_unit_columns(c, X.t.p, rows, cols, k);
+    }
+    // X = M^T column-major is M row-major; accumulate V (rows x rows)
+    Tmp X(c, {rows, cols});
+    ck(cudaMemcpyAsync(X.t.p, M, sizeof(double) * (size_t)rows * cols, cudaMemcpyDeviceToDevice,
+                       c->stream),
+       "copy");
+    Tmp V(c, {rows, rows});
+    jacobi(c, X.t.p, cols, rows, V.t.p);
+    Tmp sig(c, {rows});
+    int* perm = (int*)dalloc(c, (rows + 1) / 2 + 1);
+    ck(column_norms_sorted(c->stream, X.t.p, cols, rows, sig.t.p, perm), "norms");
+    Tmp U(c, {rows, k});
+    ck(gather_sorted_columns(c->stream, U.t.p, rows, k, nullptr, V.t.p, sig.t.p, perm), "gather");
+    c->launches += 3;
+    dfree(c, perm);
+    return U;
+  }
+  const int l = std::min(k + kOversample, std::min(rows, cols));
+  LegMap Mrow, Mcol;
+  // M(i, j) at i*cols + j
+  push(Mrow, rows, cols);
+  push(Mcol, cols, 1);
+  Tmp Om(c, {cols, l});
+  ck(gaussian_fill(c->stream, Om.t.p, (long long)cols * l, c->seed++), "gaussian");
+  ++c->launches;
+  // Y = M Omega, stored column-major (rows x l)
+  auto times_M = [&](const double* Rrow /* row-major cols x l */) {
+    Tmp Y(c, {l, rows});
+    LegMap Bk, Bn, Cm, Cn;
+    push(Bk, cols, l);
+    push(Bn, l, 1);
+    push(Cm, rows, 1);
+    push(Cn, l, rows);
+    ck(gemm_f64(c->stream, rows, l, cols, 1.0, M, Mrow, Mcol, Rrow, Bk, Bn, 0.0, Y.t.p, Cm, Cn),
+       "M Q");
+    ++c->launches;
+    return Y;
+  };
+  // Z = M^T Q (Q row-major rows x l), stored column-major (cols x l)
+  auto times_Mt = [&](const double* Qrow) {
+    Tmp Z(c, {l, cols});
+    LegMap Am, Ak, Bk, Bn, Cm, Cn;
+    push(Am, cols, 1);
+    push(Ak, rows, cols);
+    push(Bk, rows, l);
+    push(Bn, l, 1);
+    push(Cm, cols, 1);
+    push(Cn, l, cols);
+    ck(gemm_f64(c->stream, cols, l, rows, 1.0, M, Am, Ak, Qrow, Bk, Bn, 0.0, Z.t.p, Cm, Cn),
+       "M^T Q");
+    ++c->launches;
+    return Z;
+  };
+  Tmp Y = times_M(Om.t.p);
+  Om.release();
+  jacobi(c, Y.t.p, rows, l, nullptr);
+  Tmp Q = sorted_unit_columns(c, Y.t.p, rows, l, l);
+  Y.release();
+  for (int it = 0; it < kPowerIters; ++it) {
+    Tmp Z = times_Mt(Q.t.p);
+    jacobi(c, Z.t.p, cols, l, nullptr);
+    Tmp Qz = sorted_unit_columns(c, Z.t.p, cols, l, l);
+    Z.release();
+    Tmp Y2 = times_M(Qz.t.p);
+    Qz.release();
+    jacobi(c, Y2.t.p, rows, l, nullptr);
+    Q = sorted_unit_columns(c, Y2.t.p, rows, l, l);
+  }
+  // Rayleigh-Ritz: Z = M^T Q = (Q^T M)^T; Jacobi with V gives Q^T M = V S W^T
+  Tmp Z = times_Mt(Q.t.p);
+  Tmp V(c, {l, l});
+  jacobi(c, Z.t.p, cols, l, V.t.p);
+  Tmp sig(c, {l});
+  int* perm = (int*)dalloc(c, (l + 1) / 2 + 1);
+  ck(column_norms_sorted(c->stream, Z.t.p, cols, l, sig.t.p, perm), "norms");
+  Tmp Vk(c, {l, k});
+  ck(gather_sorted_columns(c->stream, Vk.t.p, l, k, nullptr, V.t.p, sig.t.p, perm), "gather");
+  c->launches += 3;
+  dfree(c, perm);
+  Ten Qv = view(Q.t, {rows, l});
+  return ein64(c, "ic,cr->ir", Qv, Vk.t);
+}
+
+// ---------------------------------------------------------------------------
+// Environment access
+// ---------------------------------------------------------------------------
+inline int slot_of(int k, int r) { return (k - 1 + r) % 4; }  // stored k-1 index
+inline int other(int x) { return 1 - x; }
+
+Ten& E(ctm_ctx* c, int kind, int k, int x, int r) { return c->env[kind][slot_of(k, r)][x]; }
+
+Ten edge_fused(const Ten& t) { return view(t, {t.dims[0], t.dims[1] * t.dims[2], t.dims[3]}); }
+
+// Write `src` as the new (kind, k, x) of frame r into its spare buffer, normalised.
+void commit(ctm_ctx* c, int kind, int k, int x, int r, const Ten& src) {
+  const int s = slot_of(k, r);
+  const int nb = 1 - c->cur[kind][s][x];
+  double* dst = c->buf[kind][s][x][nb];
+  const long long n = src.size();
+  ck(cudaMemcpyAsync(dst, src.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream), "commit");
+  ck(normalize_f64(c->stream, dst, n, c->norm_scratch, &c->flags->bad), "normalize");
+  c->launches += 2;
+  Ten t;
+  t.p = dst;
+  t.nd = src.nd;
+  for (int i = 0; i < src.nd; ++i) t.dims[i] = src.dims[i];
+  c->cur[kind][s][x] = nb;
+  c->env[kind][s][x] = t;
+}
+
+// ---------------------------------------------------------------------------
+// Moves
+// ---------------------------------------------------------------------------
+struct Proj {  // 4-index (standard) or split (sequential) isometry of one bond
+  Tmp v;       // standard: [chi, D, D, k]
+  Tmp v1, v2;  // sequential: [chi, D, c], [c, D, k]
+};
+
+const Ten& site(ctm_ctx* c, int r, int x, Ten& tmp) {
+  tmp.p = c->site[r][x];
+  tmp.nd = 5;
+  tmp.dims[0] = c->d;
+  for (int i = 1; i < 5; ++i) tmp.dims[i] = c->D;
+  return tmp;
+}
+
+const Ten dbl_layer(ctm_ctx* c, int r, int x) {
+  const int D2 = c->D * c->D;
+  if (!c->dbl[r][x]) {
+    Ten s;
+    site(c, r, x, s);
+    Tmp a = ein64(c, "puldr,pULDR->uUlLdDrR", s, s);
+    double* p = owned_alloc(c, a.t.size());
+    ck(cudaMemcpyAsync(p, a.t.p, sizeof(double) * a.t.size(), cudaMemcpyDeviceToDevice, c->stream),
+       "dbl");
+    c->dbl[r][x] = p;
+  }
+  Ten t;
+  t.p = c->dbl[r][x];
+  t.nd = 4;
+  for (int i = 0; i < 4; ++i) t.dims[i] = D2;
+  return t;
+}
+
+// Standard projector of the bond below x (Fig. 2c): v = leading left singular
+// vectors of the upper half Q = E_L E_R of the 2x2 cell with x at top-left.
+Proj projector_standard(ctm_ctx* c, int r, int x) {
+  const int y = other(x), D = c->D;
+  Ten ax = dbl_layer(c, r, x), ay = dbl_layer(c, r, y);
+  Ten C1 = E(c, 0, 1, x, r), T1 = edge_fused(E(c, 1, 1, x, r));
+  Ten T2x = edge_fused(E(c, 1, 2, x, r)), T2y = edge_fused(E(c, 1, 2, y, r));
+  Ten C2 = E(c, 0, 2, y, r), T3 = edge_fused(E(c, 1, 3, y, r));
+  Tmp EL;
+  {
+    Tmp y1 = ein64(c, "dg,gUe->dUe", C1, T2x);
+    Tmp y2 = ein64(c, "dUe,aLd->aLUe", y1, T1);
+    y1.release();
+    EL = ein64(c, "aLUe,ULXR->aXeR", y2, ax);
+  }
+  Tmp ER;
+  {
+    Tmp z1 = ein64(c, "eUz,zh->eUh", T2y, C2);
+    Tmp z2 = ein64(c, "eUh,hRb->eURb", z1, T3);
+    z1.release();
+    ER = ein64(c, "eURb,ULYR->eLbY", z2, ay);
+  }
+  Tmp Q = ein64(c, "aXeR,eRbY->aXYb", EL, ER);
+  EL.release();
+  ER.release();
+  const int na = Q.t.dims[0], nb = Q.t.dims[3];
+  const int rows = na * D * D, cols = D * D * nb;
+  const int k = std::min(c->chi, rows);
+  Proj P;
+  Tmp U = left_svd(c, Q.t.p, rows, cols, k);
+  P.v = std::move(U);
+  P.v.t = view(P.v.t, {na, D, D, k});
+  return P;
+}
+
+// Split isometries from a 4-leg network Mt[alpha, k, b, beta] (Sec. IV, Fig. 4a).
+// Also returns N = v1^T Mt (for reuse by the caller).
+void split_projector(ctm_ctx* c, const Ten& Mt, Tmp& v1, Tmp& v2, Tmp& N) {
+  const int na = Mt.dims[0], D = Mt.dims[1], nb = Mt.dims[3];
+  const int k1 = std::min(c->chip, na * D);
+  v1 = left_svd(c, Mt.p, na * D, D * nb, k1);
+  v1.t = view(v1.t, {na, D, k1});
+  N = ein64(c, "akc,akbz->cbz", v1, Mt);
+  const int k2 = std::min(c->chi, k1 * D);
+  v2 = left_svd(c, N.t.p, k1 * D, nb, k2);
+  v2.t = view(v2.t, {k1, D, k2});
+}
+
+// Sequential ket-then-bra absorption of an edge T[prev, k, b, next] with the
+// site's legs (u, l, d, r) playing the roles in `roles` ('i' in, 'o' out,
+// 'p' prev, 'n' next) (Sec. IV, Fig. 4b).  Returns [chi_p, out_k, out_b, chi_n].
+Tmp absorb_edge_seq(ctm_ctx* c, const Ten& T, const Ten& S, const char* roles, const Ten& vp1,
+                    const Ten& vp2, const Ten& vn1, const Ten& vn2) {
+  char ket[6] = {'s', 0, 0, 0, 0, 0}, bra[6] = {'s', 0, 0, 0, 0, 0};
+  for (int i = 0; i < 4; ++i) {
+    switch (roles[i]) {
+      case 'i': ket[i + 1] = 'k'; bra[i + 1] = 'b'; break;
+      case 'o': ket[i + 1] = 'o'; bra[i + 1] = 'O'; break;
+      case 'p': ket[i + 1] = 'q'; bra[i + 1] = 'Q'; break;
+      case 'n': ket[i + 1] = 'n'; bra[i + 1] = 'N'; break;
+      default: fail(CTM_ERR_ARG, "internal: bad role");
+    }
+  }
+  char spec[64];
+  Tmp X1 = ein(c, "AkbB,Bnc->Akbnc", T, vn1);
+  std::snprintf(spec, sizeof spec, "Akbnc,%s->Abcsoq", ket);
+  Tmp X2 = ein(c, spec, X1, S);
+  X1.release();
+  Tmp X3 = ein(c, "Abcsoq,Aqe->bcsoe", X2, vp1);
+  X2.release();
+  Tmp X4 = ein(c, "bcsoe,cNy->bsoeNy", X3, vn2);
+  X3.release();
+  std::snprintf(spec, sizeof spec, "bsoeNy,%s->oeyOQ", bra);
+  Tmp X5 = ein(c, spec, X4, S);
+  X4.release();
+  return ein(c, "oeyOQ,eQx->xoOy", X5, vp2);
+}
+
+// Reduced-network projector of the bond below x (Sec. III-IV, Fig. 3c, Fig. 8).
+Proj projector_seq(ctm_ctx* c, int r, int x) {
+  Ten S;
+  site(c, r, x, S);
+  Ten C1 = E(c, 0, 1, x, r), T1 = E(c, 1, 1, x, r);
+  Ten C2 = E(c, 0, 2, x, r), T3 = E(c, 1, 3, x, r);
+  Ten T2 = E(c, 1, 2, x, r);
+  Tmp vl1, vl2, Nl, vr1, vr2, Nr;
+  {
+    Tmp L = ein64(c, "dg,akbd->gkba", C1, T1);
+    split_projector(c, L, vl1, vl2, Nl);
+  }
+  {
+    Tmp R = ein64(c, "ez,zkbw->ekbw", C2, T3);
+    split_projector(c, R, vr1, vr2, Nr);
+  }
+  Tmp C1p = ein64(c, "cby,cba->ya", vl2, Nl);
+  Tmp C2p = ein64(c, "cby,cbw->yw", vr2, Nr);
+  Nl.release();
+  Nr.release();
+  // T'2: the top edge with x absorbed, left bond by v_l, right bond by v_r
+  Tmp T2p = absorb_edge_seq(c, T2, S, "ipon", vl1, vl2, vr1, vr2);
+  Tmp Xm = ein64(c, "ya,ykbz->akbz", C1p, T2p);
+  T2p.release();
+  Tmp M = ein64(c, "akbz,zw->akbw", Xm, C2p);
+  Xm.release();
+  Proj P;
+  Tmp N;
+  split_projector(c, M, P.v1, P.v2, N);
+  return P;
+}
+
+// One column absorption in frame r (Sec. II, Fig. 2a-b).
+void column_absorb(ctm_ctx* c, int r, int mode) {
+  Proj P[2];
+  for (int x = 0; x < 2; ++x)
+    P[x] = (mode == CTM_STANDARD) ? projector_standard(c, r, x) : projector_seq(c, r, x);
+  Tmp newT[2], newC1[2], newC4[2];
+  for (int x = 0; x < 2; ++x) {
+    const int y = other(x);
+    Ten C1 = E(c, 0, 1, x, r), T2 = E(c, 1, 2, x, r), T1 = E(c, 1, 1, x, r);
+    Ten C4 = E(c, 0, 4, x, r), T4 = E(c, 1, 4, x, r);
+    Ten S;
+    site(c, r, x, S);
+    Tmp Xc = ein(c, "dg,gkbe->dkbe", C1, T2);
+    Tmp Xc4 = ein(c, "lu,rkbl->rukb", C4, T4);
+    if (mode == CTM_STANDARD) {
+      const Proj& vb = P[x];
+      const Proj& vt = P[y];
+      const int D2 = c->D * c->D;
+      Ten ax = dbl_layer(c, r, x);
+      Ten vtf = view(vt.v.t, {vt.v.t.dims[0], D2, vt.v.t.dims[3]});
+      Ten vbf = view(vb.v.t, {vb.v.t.dims[0], D2, vb.v.t.dims[3]});
+      Tmp W1 = ein(c, "aLu,uUn->aLUn", edge_fused(T1), vtf);
+      Tmp W2 = ein(c, "aLUn,ULXR->anXR", W1, ax);
+      W1.release();
+      Tmp Tn = ein(c, "anXR,aXp->pRn", W2, vbf);
+      newT[y] = std::move(Tn);
+      newT[y].t = view(newT[y].t, {newT[y].t.dims[0], c->D, c->D, newT[y].t.dims[2]});
+      newC1[y] = ein(c, "dkbe,dkby->ye", Xc, vt.v);
+      newC4[y] = ein(c, "rukb,ukby->ry", Xc4, vb.v);
+    } else {
+      const Proj& vb = P[x];
+      const Proj& vt = P[y];
+      newT[y] = absorb_edge_seq(c, T1, S, "nipo", vb.v1, vb.v2, vt.v1, vt.v2);
+      Tmp X2 = ein(c, "dkc,dkbe->cbe", vt.v1, Xc);
+      newC1[y] = ein(c, "cby,cbe->ye", vt.v2, X2);
+      Tmp W = ein(c, "rukb,ukc->rcb", Xc4, vb.v1);
+      newC4[y] = ein(c, "rcb,cby->ry", W, vb.v2);
+    }
+  }
+  for (int y = 0; y < 2; ++y) {
+    commit(c, 1, 1, y, r, newT[y]);
+    commit(c, 0, 1, y, r, newC1[y]);
+    commit(c, 0, 4, y, r, newC4[y]);
+  }
+}
+
+void check_flags(ctm_ctx* c) {
+  DevFlags h;
+  ck(cudaMemcpyAsync(&h, c->flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, c->stream), "flags");
+  ck(cudaStreamSynchronize(c->stream), "sync");
+  if (h.error || h.noconv || h.bad) {
+    ck(cudaMemsetAsync(c->flags, 0, sizeof(DevFlags), c->stream), "flags reset");
+    if (h.error) fail(CTM_ERR_CUDA, "a grid barrier timed out");
+    if (h.bad) fail(CTM_ERR_NAN, "a new environment tensor was zero or not finite");
+    fail(CTM_ERR_NOCONV, "a Jacobi SVD reached its sweep cap");
+  }
+}
+
+void do_move(ctm_ctx* c, int dir, int mode) {
+  column_absorb(c, dir, mode);
+  column_absorb(c, dir, mode);
+  check_flags(c);
+}
+
+bool all_bonds_at(ctm_ctx* c, int target) {
+  for (int kind = 0; kind < 2; ++kind)
+    for (int k = 0; k < 4; ++k)
+      for (int x = 0; x < 2; ++x) {
+        const Ten& t = c->env[kind][k][x];
+        if (t.dims[0] < target || t.dims[t.nd - 1] < target) return false;
+      }
+  return true;
+}
+
+std::vector<int> all_dims(ctm_ctx* c) {
+  std::vector<int> v;
+  for (int kind = 0; kind < 2; ++kind)
+    for (int k = 0; k < 4; ++k)
+      for (int x = 0; x < 2; ++x) {
+        const Ten& t = c->env[kind][k][x];
+        for (int i = 0; i < t.nd; ++i) v.push_back(t.dims[i]);
+      }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Initial environment
+// ---------------------------------------------------------------------------
+void fold_init(ctm_ctx* c) {
+  const int D = c->D, D2 = D * D;
+  Ten bnd;
+  bnd.p = c->bnd;
+  bnd.nd = 2;
+  bnd.dims[0] = bnd.dims[1] = D;
+  for (int k = 1; k <= 4; ++k)
+    for (int x = 0; x < 2; ++x) {
+      Ten Sx, Sy;
+      site(c, k - 1, x, Sx);
+      site(c, k - 1, other(x), Sy);
+      Tmp X1 = ein64(c, "puldr,uU->pldrU", Sx, bnd);
+      Tmp X2 = ein64(c, "pldrU,lL->pdrUL", X1, bnd);
+      Tmp Cc = ein64(c, "pdrUL,pULDR->dDrR", X2, Sx);
+      Cc.t = view(Cc.t, {D2, D2});
+      commit(c, 0, k, x, 0, Cc);
+      Tmp Y1 = ein64(c, "puldr,lL->pudrL", Sy, bnd);
+      Tmp Tt = ein64(c, "pudrL,pULDR->dDrRuU", Y1, Sy);
+      Tt.t = view(Tt.t, {D2, D, D, D2});
+      commit(c, 1, k, x, 0, Tt);
+    }
+}
+
+void grow(ctm_ctx* c) {
+  for (int it = 0; it < 16 && !all_bonds_at(c, c->chi); ++it) {
+    std::vector<int> before = all_dims(c);
+    for (int dir = 0; dir < 4; ++dir) do_move(c, dir, CTM_STANDARD);
+    if (all_dims(c) == before) break;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Observables
+// ---------------------------------------------------------------------------
+std::vector<double> spectrum(ctm_ctx* c, const Ten& C) {
+  // singular values of the corner via one-sided Jacobi on its columns (or rows)
+  int n1 = C.dims[0], n2 = C.dims[1];
+  const bool cols_side = n2 <= n1;
+  const int nrows = cols_side ? n1 : n2, ncols = cols_side ? n2 : n1;
+  Tmp X(c, {ncols, nrows});
+  LegMap m;
+  if (cols_side) {  // X col-major = C columns: X[j*n1 + i] = C[i*n2 + j]
+    push(m, n2, 1);
+    push(m, n1, n2);
+    ck(permute_f64(c->stream, X.t.p, C.p, m), "transpose");
+    ++c->launches;
+  } else {
+    ck(cudaMemcpyAsync(X.t.p, C.p, sizeof(double) * C.size(), cudaMemcpyDeviceToDevice, c->stream),
+       "copy");
+  }
+  jacobi(c, X.t.p, nrows, ncols, nullptr);
+  Tmp sig(c, {ncols});
+  int* perm = (int*)dalloc(c, (ncols + 1) / 2 + 1);
+  ck(column_norms_sorted(c->stream, X.t.p, nrows, ncols, sig.t.p, perm), "norms");
+  c->launches += 2;
+  std::vector<double> s(ncols);
+  std::vector<int> hp(ncols);
+  ck(cudaMemcpyAsync(s.data(), sig.t.p, sizeof(double) * ncols, cudaMemcpyDeviceToHost, c->stream),
+     "d2h");
+  ck(cudaMemcpyAsync(hp.data(), perm, sizeof(int) * ncols, cudaMemcpyDeviceToHost, c->stream), "d2h");
+  dfree(c, perm);
+  check_flags(c);
+  std::vector<double> out(ncols);
+  double ss = 0.0;
+  for (int i = 0; i < ncols; ++i) {
+    out[i] = s[hp[i]];
+    ss += out[i] * out[i];
+  }
+  const double nrm = std::sqrt(ss);
+  if (!(nrm > 0.0)) fail(CTM_ERR_NAN, "zero corner");
+  for (double& v : out) v /= nrm;
+  return out;
+}
+
+double scalar_of(ctm_ctx* c, const Ten& t) {
+  double v = 0.0;
+  ck(cudaMemcpyAsync(&v, t.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "d2h");
+  ck(cudaStreamSynchronize(c->stream), "sync");
+  return v;
+}
+
+double expect_bond(ctm_ctx* c, int bond, const double* op_host) {
+  const int r = (bond >= 2) ? 1 : 0;
+  const int x = bond & 1, y = other(x);
+  const int d = c->d, D2 = c->D * c->D;
+  Ten Sx, Sy;
+  site(c, r, x, Sx);
+  site(c, r, y, Sy);
+  Tmp ax = ein64(c, "puldr,PULDR->pPuUlLdDrR", Sx, Sx);
+  Tmp ay = ein64(c, "puldr,PULDR->pPuUlLdDrR", Sy, Sy);
+  Ten axv = view(ax.t, {d, d, D2, D2, D2, D2}), ayv = view(ay.t, {d, d, D2, D2, D2, D2});
+  Tmp left;
+  {
+    Tmp e1 = ein64(c, "dg,gUe->dUe", E(c, 0, 1, x, r), edge_fused(E(c, 1, 2, x, r)));
+    Tmp e2 = ein64(c, "dUe,mLd->mLUe", e1, edge_fused(E(c, 1, 1, x, r)));
+    Tmp e3 = ein64(c, "mLUe,lm->lLUe", e2, E(c, 0, 4, x, r));
+    Tmp e4 = ein64(c, "lLUe,kXl->kXLUe", e3, edge_fused(E(c, 1, 4, x, r)));
+    left = ein64(c, "kXLUe,pPULXR->eRkpP", e4, axv);
+  }
+  Tmp right;
+  {
+    Tmp f1 = ein64(c, "eVz,zh->eVh", edge_fused(E(c, 1, 2, y, r)), E(c, 0, 2, y, r));
+    Tmp f2 = ein64(c, "eVh,hWt->eVWt", f1, edge_fused(E(c, 1, 3, y, r)));
+    Tmp f3 = ein64(c, "eVWt,ti->eVWi", f2, E(c, 0, 3, y, r));
+    Tmp f4 = ein64(c, "eVWi,iYk->eVWYk", f3, edge_fused(E(c, 1, 4, y, r)));
+    right = ein64(c, "eVWYk,qQVRYW->eRkqQ", f4, ayv);
+  }
+  Tmp rho = ein64(c, "eRkpP,eRkqQ->pqPQ", left, right);
+  Ten rv = view(rho.t, {d * d, d * d});
+  Tmp op(c, {d * d, d * d});
+  ck(cudaMemcpyAsync(op.t.p, op_host, sizeof(double) * d * d * d * d, cudaMemcpyHostToDevice,
+                     c->stream),
+     "h2d");
+  Tmp num = ein64(c, "ij,ji->", rv, op.t);
+  Tmp I = identity(c, d * d);
+  Tmp den = ein64(c, "ij,ji->", rv, I.t);
+  const double n = scalar_of(c, num.t), dd = scalar_of(c, den.t);
+  return n / dd;
+}
+
+double log_kappa(ctm_ctx* c) {
+  const int x = 0, y = 1, r = 0;
+  auto C = [&](int k, int s) { return E(c, 0, k, s, r); };
+  auto T = [&](int k, int s) { return edge_fused(E(c, 1, k, s, r)); };
+  // Z00
+  Tmp a1 = ein64(c, "ab,bc->ac", C(1, x), C(2, y));
+  Tmp a2 = ein64(c, "ac,cd->ad", a1, C(3, x));
+  Tmp z00 = ein64(c, "ad,da->", a2, C(4, y));
+  // Z20: C1x C2y T3y T3x C3x C4y T1y T1x
+  Tmp b1 = ein64(c, "ab,bc->ac", C(1, x), C(2, y));
+  Tmp b2 = ein64(c, "ac,cKd->aKd", b1, T(3, y));
+  Tmp b3 = ein64(c, "aKd,dLe->aKLe", b2, T(3, x));
+  Tmp b4 = ein64(c, "aKLe,ef->aKLf", b3, C(3, x));
+  Tmp b5 = ein64(c, "aKLf,fg->aKLg", b4, C(4, y));
+  Tmp b6 = ein64(c, "aKLg,gLh->aKh", b5, T(1, y));
+  Tmp z20 = ein64(c, "aKh,hKa->", b6, T(1, x));
+  // Z02: C1x T2x T2y C2y C3x T4x T4y C4y
+  Tmp c1 = ein64(c, "ab,bKc->aKc", C(1, x), T(2, x));
+  Tmp c2 = ein64(c, "aKc,cLd->aKLd", c1, T(2, y));
+  Tmp c3 = ein64(c, "aKLd,de->aKLe", c2, C(2, y));
+  Tmp c4 = ein64(c, "aKLe,ef->aKLf", c3, C(3, x));
+  Tmp c5 = ein64(c, "aKLf,fLg->aKg", c4, T(4, x));
+  Tmp c6 = ein64(c, "aKg,gKh->ah", c5, T(4, y));
+  Tmp z02 = ein64(c, "ah,ha->", c6, C(4, y));
+  // Z22 as an upper and a lower row
+  Ten ax = dbl_layer(c, r, x), ay = dbl_layer(c, r, y);
+  Tmp e1 = ein64(c, "dg,gPc->dPc", C(1, x), T(2, x));
+  Tmp e2 = ein64(c, "dPc,lWd->lWPc", e1, T(1, x));
+  Tmp e3 = ein64(c, "lWPc,PWXY->lcXY", e2, ax);
+  Tmp f1 = ein64(c, "cQe,eh->cQh", T(2, y), C(2, y));
+  Tmp f2 = ein64(c, "cQh,hRf->cQRf", f1, T(3, y));
+  Tmp f3 = ein64(c, "cQRf,QYZR->cfYZ", f2, ay);
+  Tmp up = ein64(c, "lcXY,cfYZ->lXfZ", e3, f3);
+  Tmp g1 = ein64(c, "jk,kVl->jVl", C(4, y), T(1, y));
+  Tmp g2 = ein64(c, "jVl,iUj->iUVl", g1, T(4, y));
+  Tmp g3 = ein64(c, "iUVl,XVUN->ilXN", g2, ay);
+  Tmp h1 = ein64(c, "gh,hTi->gTi", C(3, x), T(4, x));
+  Tmp h2 = ein64(c, "gTi,fSg->fSTi", h1, T(3, x));
+  Tmp h3 = ein64(c, "fSTi,ZNTS->fiZN", h2, ax);
+  Tmp low = ein64(c, "ilXN,fiZN->lXfZ", g3, h3);
+  Tmp z22 = ein64(c, "lXfZ,lXfZ->", up, low);
+  const double v22 = scalar_of(c, z22.t), v00 = scalar_of(c, z00.t);
+  const double v20 = scalar_of(c, z20.t), v02 = scalar_of(c, z02.t);
+  const double ratio = v22 * v00 / (v20 * v02);
+  if (!(ratio > 0.0) || !std::isfinite(ratio)) fail(CTM_ERR_NAN, "non-positive norm ratio");
+  return 0.25 * std::log(ratio);
+}
+
+template <class F>
+int guarded(ctm_ctx* c, F&& f) {
+  try {
+    f();
+    if (c) c->err.clear();
+    return CTM_OK;
+  } catch (const CtmError& e) {
+    if (c) c->err = e.msg;
+    return e.code;
+  } catch (const std::exception& e) {
+    if (c) c->err = e.what();
+    return CTM_ERR_OOM;
+  }
+}
+
+void copy_in(ctm_ctx* c, double* dst, const double* src, size_t n) {
+  cudaPointerAttributes at;
+  cudaMemcpyKind kind = cudaMemcpyHostToDevice;
+  if (cudaPointerGetAttributes(&at, src) == cudaSuccess &&
+      (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged))
+    kind = cudaMemcpyDeviceToDevice;
+  cudaGetLastError();
+  ck(cudaMemcpyAsync(dst, src, sizeof(double) * n, kind, c->stream), "copy in");
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int ctm_init_env(ctm_ctx** out, const double* A, const double* B, int d, int D, int chi,
+                 int chi_prime, int precision, const double* boundary, void* stream) {
+  if (!out || !A || !B || d < 1 || D < 1 || chi < 1 || chi_prime < 0) return CTM_ERR_ARG;
+  if (precision != CTM_FP64 && precision != CTM_TF32 && precision != CTM_BF16) return CTM_ERR_ARG;
+  if ((long long)chi * D * D * chi > (1ll << 31)) return CTM_ERR_ARG;
+  *out = nullptr;
+  ctm_ctx* c = new (std::nothrow) ctm_ctx;
+  if (!c) return CTM_ERR_OOM;
+  c->stream = (cudaStream_t)stream;
+  c->d = d;
+  c->D = D;
+  c->chi = chi;
+  c->chip = chi_prime > 0 ? chi_prime : chi;
+  c->precision = precision;
+  int rc = guarded(c, [&] {
+    int dev = 0;
+    ck(cudaGetDevice(&dev), "device");
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      unsigned long long thr = ~0ull;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    void* f = nullptr;
+    ck(cudaMalloc(&f, sizeof(DevFlags)), "flags");
+    c->owned.push_back(f);
+    c->flags = (DevFlags*)f;
+    ck(cudaMemsetAsync(c->flags, 0, sizeof(DevFlags), c->stream), "flags");
+    c->norm_scratch = owned_alloc(c, kNormScratch);
+    if (precision != CTM_FP64) {
+      c->tc = tc_create();
+      if (!c->tc) fail(CTM_ERR_UNSUPPORTED, "tensor-core GEMM unavailable");
+    }
+    const long long ns = (long long)d * D * D * D * D;
+    for (int r = 0; r < 4; ++r)
+      for (int x = 0; x < 2; ++x) c->site[r][x] = owned_alloc(c, ns);
+    copy_in(c, c->site[0][0], A, ns);
+    copy_in(c, c->site[0][1], B, ns);
+    // rot(A)[p, a1, a2, a3, a4] = A[p, a2, a3, a4, a1]
+    LegMap m;
+    const long long D4 = (long long)D * D * D * D, D3 = (long long)D * D * D;
+    push(m, d, D4);
+    push(m, D, 1);
+    push(m, D, D3);
+    push(m, D, (long long)D * D);
+    push(m, D, D);
+    for (int r = 1; r < 4; ++r)
+      for (int x = 0; x < 2; ++x) {
+        ck(permute_f64(c->stream, c->site[r][x], c->site[r - 1][x], m), "rotate");
+        ++c->launches;
+      }
+    c->bnd = owned_alloc(c, (long long)D * D);
+    if (boundary) {
+      copy_in(c, c->bnd, boundary, (size_t)D * D);
+    } else {
+      ck(fill_identity(c->stream, c->bnd, D), "identity");
+      ++c->launches;
+    }
+    const int cmax = std::max(chi, D * D);
+    for (int kind = 0; kind < 2; ++kind)
+      for (int k = 0; k < 4; ++k)
+        for (int x = 0; x < 2; ++x)
+          for (int b = 0; b < 2; ++b)
+            c->buf[kind][k][x][b] =
+                owned_alloc(c, kind == 0 ? (long long)cmax * cmax : (long long)cmax * D * D * cmax);
+    fold_init(c);
+    check_flags(c);
+    grow(c);
+  });
+  if (rc != CTM_OK) {
+    ctm_free(c);
+    return rc;
+  }
+  *out = c;
+  return CTM_OK;
+}
+
+int ctm_move(ctm_ctx* c, int dir, int mode) {
+  if (!c || dir < 0 || dir > 3 || (mode != CTM_STANDARD && mode != CTM_REDUCED_SEQUENTIAL))
+    return CTM_ERR_ARG;
+  return guarded(c, [&] { do_move(c, dir, mode); });
+}
+
+int ctm_converge(ctm_ctx* c, int mode, int max_iter, double tol, int* iters_done,
+                 double* last_delta) {
+  if (!c || max_iter < 1 || (mode != CTM_STANDARD && mode != CTM_REDUCED_SEQUENTIAL))
+    return CTM_ERR_ARG;
+  bool converged = false;
+  int rc = guarded(c, [&] {
+    std::vector<std::vector<double>> old;
+    for (int i = 0; i < 8; ++i) old.push_back(spectrum(c, c->env[0][i / 2][i % 2]));
+    double delta = INFINITY;
+    int it = 0;
+    for (it = 1; it <= max_iter; ++it) {
+      for (int dir = 0; dir < 4; ++dir) do_move(c, dir, mode);
+      delta = 0.0;
+      for (int i = 0; i < 8; ++i) {
+        std::vector<double> s = spectrum(c, c->env[0][i / 2][i % 2]);
+        const size_t n = std::max(s.size(), old[i].size());
+        double acc = 0.0;
+        for (size_t j = 0; j < n; ++j) {
+          const double a = j < s.size() ? s[j] : 0.0, b = j < old[i].size() ? old[i][j] : 0.0;
+          acc += (a - b) * (a - b);
+        }
+        delta = std::max(delta, std::sqrt(acc));
+        old[i] = std::move(s);
+      }
+      if (delta < tol) {
+        converged = true;
+        break;
+      }
+    }
+    if (iters_done) *iters_done = std::min(it, max_iter);
+    if (last_delta) *last_delta = delta;
+  });
+  if (rc == CTM_OK && !converged) {
+    c->err = "max_iter reached";
+    return CTM_ERR_NOCONV;
+  }
+  return rc;
+}
+
+int ctm_expect_bond(ctm_ctx* c, int bond, const double* op, double* value) {
+  if (!c || bond < 0 || bond > 3 || !op || !value) return CTM_ERR_ARG;
+  return guarded(c, [&] { *value = expect_bond(c, bond, op); });
+}
+
+int ctm_corner_spectrum(ctm_ctx* c, int corner, double* s, int* len) {
+  if (!c || corner < 0 || corner > 7 || !s || !len) return CTM_ERR_ARG;
+  return guarded(c, [&] {
+    std::vector<double> v = spectrum(c, c->env[0][corner / 2][corner % 2]);
+    for (size_t i = 0; i < v.size(); ++i) s[i] = v[i];
+    *len = (int)v.size();
+  });
+}
+
+int ctm_log_kappa(ctm_ctx* c, double* value) {
+  if (!c || !value) return CTM_ERR_ARG;
+  return guarded(c, [&] { *value = log_kappa(c); });
+}
+
+int ctm_get_tensor(ctm_ctx* c, int kind, int k, int x, double* out, int* dims) {
+  if (!c || kind < 0 || kind > 1 || k < 1 || k > 4 || x < 0 || x > 1 || !dims) return CTM_ERR_ARG;
+  return guarded(c, [&] {
+    const Ten& t = c->env[kind][k - 1][x];
+    for (int i = 0; i < 4; ++i) dims[i] = i < t.nd ? t.dims[i] : 0;
+    if (out) {
+      ck(cudaMemcpyAsync(out, t.p, sizeof(double) * t.size(), cudaMemcpyDeviceToHost, c->stream),
+         "d2h");
+      ck(cudaStreamSynchronize(c->stream), "sync");
+    }
+  });
+}
+
+int ctm_set_tensor(ctm_ctx* c, int kind, int k, int x, const double* in, const int* dims) {
+  if (!c || kind < 0 || kind > 1 || k < 1 || k > 4 || x < 0 || x > 1 || !in || !dims)
+    return CTM_ERR_ARG;
+  const int nd = kind == 0 ? 2 : 4;
+  const int cmax = std::max(c->chi, c->D * c->D);
+  if (dims[0] < 1 || dims[0] > cmax || dims[nd - 1] < 1 || dims[nd - 1] > cmax) return CTM_ERR_ARG;
+  if (nd == 4 && (dims[1] != c->D || dims[2] != c->D)) return CTM_ERR_ARG;
+  return guarded(c, [&] {
+    Ten& t = c->env[kind][k - 1][x];
+    t.nd = nd;
+    for (int i = 0; i < nd; ++i) t.dims[i] = dims[i];
+    ck(cudaMemcpyAsync(t.p, in, sizeof(double) * t.size(), cudaMemcpyHostToDevice, c->stream),
+       "h2d");
+    ck(cudaStreamSynchronize(c->stream), "sync");
+  });
+}
+
+long long ctm_kernel_launches(ctm_ctx* c) { return c ? c->launches : 0; }
+
+const char* ctm_last_error(ctm_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+void ctm_free(ctm_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (void* p : c->owned) cudaFree(p);
+  if (c->tc) tc_destroy(c->tc);
+  cudaGetLastError();
+  delete c;
+}
+
+}  // extern "C"

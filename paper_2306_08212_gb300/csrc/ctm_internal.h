@@ -1,0 +1,111 @@
+// Internal declarations shared by the libctm translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+namespace ctm {
+
+constexpr int kMaxLegs = 12;
+
+// A composite index over up to kMaxLegs sub-legs (row-major, last fastest);
+// its memory offset is sum_l idx_l * stride_l.  Any leg permutation of a
+// row-major tensor splits into an M-part and a K-part whose offsets add, so a
+// GEMM operand can be read in any leg order without a transpose pass.
+struct LegMap {
+  int n = 0;
+  int dim[kMaxLegs];
+  long long stride[kMaxLegs];
+  long long extent() const {
+    long long e = 1;
+    for (int i = 0; i < n; ++i) e *= dim[i];
+    return e;
+  }
+};
+
+// FP64 tensor view (device memory, row-major contiguous).
+struct Ten {
+  double* p = nullptr;
+  int nd = 0;
+  int dims[kMaxLegs] = {0};
+  long long size() const {
+    long long s = 1;
+    for (int i = 0; i < nd; ++i) s *= dims[i];
+    return s;
+  }
+  int rows_first(int nrow_legs) const {  // product of the first nrow_legs dims
+    int r = 1;
+    for (int i = 0; i < nrow_legs; ++i) r *= dims[i];
+    return r;
+  }
+};
+
+struct Status {
+  int code = 0;
+  std::string msg;
+};
+
+// Device-side error/status words of one context (zeroed at creation).
+// The first block (barrier state and sweep maxima) is reset before every
+// cooperative launch; the sticky words after it are cleared only by the host
+// once it has read them.
+struct DevFlags {
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  unsigned long long off_max[2];  // per-sweep max off-diagonal cosine (bits of a double >= 0)
+  int error;                      // sticky: a grid barrier timed out
+  int noconv;                     // sticky: a Jacobi sweep cap was reached
+  int bad;                        // sticky: a normalised tensor was zero or not finite
+  int sweeps;                     // sweeps used by the last Jacobi launch
+};
+constexpr size_t kDevFlagsResetBytes = 24;  // offsetof(DevFlags, error)
+
+// ---- kernels (gemm_f64.cu) ----
+// C(m,n) = alpha * sum_k A(m,k) B(k,n) + beta * C(m,n), all FP64, every operand
+// addressed through LegMaps.
+cudaError_t gemm_f64(cudaStream_t s, long long M, long long N, long long K, double alpha,
+                     const double* A, const LegMap& Am, const LegMap& Ak, const double* B,
+                     const LegMap& Bk, const LegMap& Bn, double beta, double* C,
+                     const LegMap& Cm, const LegMap& Cn);
+
+// out[i] = in[map(i)] (gather permute), i over map.extent().
+cudaError_t permute_f64(cudaStream_t s, double* out, const double* in, const LegMap& map);
+
+// ---- linear algebra (linalg.cu) ----
+
+// Fill x[0..n) with N(0,1) samples from a counter-based generator (SplitMix64
+// hashing of (seed, index), Box-Muller); deterministic in (seed, n).
+cudaError_t gaussian_fill(cudaStream_t s, double* x, long long n, unsigned long long seed);
+
+// One-sided Jacobi (Hestenes) on the columns of X (nrows x ncols, column-major,
+// leading dimension nrows), optionally accumulating the rotations in V
+// (ncols x ncols column-major, initialised to the identity here).  On return
+// the columns of X are mutually orthogonal.  Cooperative launch with a bounded
+// grid barrier.  Returns 0, or CTM_ERR_NOCONV / CTM_ERR_CUDA style codes.
+int jacobi_onesided(cudaStream_t s, double* X, int nrows, int ncols, double* V,
+                    DevFlags* flags, int max_sweeps, long long* launches);
+
+// Column norms of X (nrows x ncols col-major) into sig[ncols]; perm[r] = index of
+// the r-th largest.  Single-block kernels.
+cudaError_t column_norms_sorted(cudaStream_t s, const double* X, int nrows, int ncols,
+                                double* sig, int* perm);
+
+// U(row-major rows x k)[i, r] = X[perm[r]][i] / sig[perm[r]]  (normalise)   when V == nullptr
+//                             = V[perm[r]][i]                 (accumulated) otherwise
+// followed by the sign convention (largest-|entry| of each column positive).
+cudaError_t gather_sorted_columns(cudaStream_t s, double* U, int rows, int k, const double* X,
+                                  const double* V, const double* sig, const int* perm);
+
+// x /= ||x||_F with a deterministic two-level reduction; scratch holds
+// kNormScratch doubles (partials, then the norm at scratch[kNormScratch - 1]);
+// sets *bad = 1 (device) if the norm is zero or not finite.
+constexpr int kNormScratch = 305;
+cudaError_t normalize_f64(cudaStream_t s, double* x, long long n, double* scratch, int* bad);
+
+cudaError_t fill_identity(cudaStream_t s, double* x, int n);
+
+}  // namespace ctm

@@ -1,0 +1,363 @@
+// FP64 dense linear algebra for the projector factorisations: one-sided
+// (Hestenes) Jacobi SVD with a parallel round-robin ordering, sorting and
+// gathering of singular vectors, Frobenius normalisation, and a counter-based
+// Gaussian generator for randomized range finding.
+//
+// Methods: one-sided Jacobi with the Rutishauser rotation and the
+// cosine-based stopping rule (Demmel & Veselic, SIAM J. Matrix Anal. Appl. 13,
+// 1204 (1992)); round-robin ("chess tournament") pair ordering (Brent & Luk,
+// SIAM J. Sci. Stat. Comput. 6, 69 (1985)); SplitMix64 (Steele, Lea & Flood,
+// OOPSLA 2014) with the Box-Muller transform.
+#include "ctm_internal.h"
+
+#include <cmath>
+#include <cstddef>
+
+namespace ctm {
+
+static_assert(offsetof(DevFlags, error) == kDevFlagsResetBytes, "DevFlags layout");
+
+// ---------------------------------------------------------------------------
+// Bounded grid barrier for cooperative launches.  Every wait has an iteration
+// cap; on timeout the kernel records an error and all blocks return.
+// ---------------------------------------------------------------------------
+constexpr long long kBarrierSpinLimit = 1ll << 24;  // x ~64 ns sleeps: about a second
+
+__device__ __forceinline__ bool grid_barrier(DevFlags* fl, unsigned nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &fl->bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&fl->bar_count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&fl->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&fl->bar_gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == g) {
+        if (++spins > kBarrierSpinLimit) {
+          atomicExch(&fl->error, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = (*(volatile int*)&fl->error) == 0;
+  }
+  __syncthreads();
+  return s_ok;
+}
+
+template <int NT>
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c) {
+  __shared__ double red[3][NT / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+  }
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  __syncthreads();
+  if (l == 0) {
+    red[0][w] = a;
+    red[1][w] = b;
+    red[2][w] = c;
+  }
+  __syncthreads();
+  a = b = c = 0.0;
+  for (int i = 0; i < NT / 32; ++i) {  // fixed order: deterministic
+    a += red[0][i];
+    b += red[1][i];
+    c += red[2][i];
+  }
+}
+
+constexpr int kJacobiThreads = 256;
+
+// Column held at round-robin position p during step s (n even, position 0 fixed).
+__device__ __forceinline__ int rr_col(int p, int s, int n) {
+  return p == 0 ? 0 : 1 + (p - 1 + s) % (n - 1);
+}
+
+__global__ void __launch_bounds__(kJacobiThreads)
+jacobi_kernel(double* __restrict__ X, int nrows, int ncols, int npad, double* __restrict__ V,
+              DevFlags* fl, int max_sweeps, double tol) {
+  const unsigned nblocks = gridDim.x;
+  const int npairs = npad / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double local_max = 0.0;
+    for (int step = 0; step < npad - 1; ++step) {
+      for (int k = blockIdx.x; k < npairs; k += gridDim.x) {
+        int i = rr_col(k, step, npad);
+        int j = rr_col(npad - 1 - k, step, npad);
+        if (i >= ncols || j >= ncols) continue;
+        if (i > j) {
+          const int t = i;
+          i = j;
+          j = t;
+        }
+        double* xi = X + (long long)i * nrows;
+        double* xj = X + (long long)j * nrows;
+        double a = 0.0, b = 0.0, g = 0.0;
+        for (int r = threadIdx.x; r < nrows; r += kJacobiThreads) {
+          const double u = xi[r], v = xj[r];
+          a = fma(u, u, a);
+          b = fma(v, v, b);
+          g = fma(u, v, g);
+        }
+        block_sum3<kJacobiThreads>(a, b, g);
+        if (a == 0.0 || b == 0.0) continue;
+        const double cosang = fabs(g) / (sqrt(a) * sqrt(b));
+        local_max = fmax(local_max, cosang);
+        if (!(cosang > tol)) continue;
+        const double zeta = (b - a) / (2.0 * g);
+        const double t = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t);
+        const double sn = c * t;
+        for (int r = threadIdx.x; r < nrows; r += kJacobiThreads) {
+          const double u = xi[r], v = xj[r];
+          xi[r] = c * u - sn * v;
+          xj[r] = sn * u + c * v;
+        }
+        if (V) {
+          double* vi = V + (long long)i * ncols;
+          double* vj = V + (long long)j * ncols;
+          for (int r = threadIdx.x; r < ncols; r += kJacobiThreads) {
+            const double u = vi[r], v = vj[r];
+            vi[r] = c * u - sn * v;
+            vj[r] = sn * u + c * v;
+          }
+        }
+        __syncthreads();
+      }
+      if (!grid_barrier(fl, nblocks)) return;
+      // every block has read the previous sweep's slot before this barrier, so
+      // the slot of the next sweep can be cleared now
+      if (step == 0 && blockIdx.x == 0 && threadIdx.x == 0)
+        atomicExch(&fl->off_max[(sweep + 1) & 1], 0ull);
+    }
+    if (threadIdx.x == 0 && local_max > 0.0)
+      atomicMax(&fl->off_max[sweep & 1], (unsigned long long)__double_as_longlong(local_max));
+    if (!grid_barrier(fl, nblocks)) return;
+    const double m = __longlong_as_double(
+        (long long)(*(volatile unsigned long long*)&fl->off_max[sweep & 1]));
+    if (!(m > tol)) {  // converged (all blocks read the same value)
+      if (blockIdx.x == 0 && threadIdx.x == 0) fl->sweeps = sweep + 1;
+      return;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    fl->sweeps = max_sweeps;
+    atomicExch(&fl->noconv, 1);
+  }
+}
+
+__global__ void identity_kernel(double* x, int n) {
+  const long long nn = (long long)n * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] = (i / n == i % n) ? 1.0 : 0.0;
+}
+
+cudaError_t fill_identity(cudaStream_t s, double* x, int n) {
+  long long blocks = ((long long)n * n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  identity_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, n);
+  return cudaGetLastError();
+}
+
+int jacobi_onesided(cudaStream_t s, double* X, int nrows, int ncols, double* V, DevFlags* flags,
+                    int max_sweeps, long long* launches) {
+  if (ncols < 2) {
+    if (V && ncols == 1) {
+      if (fill_identity(s, V, 1) != cudaSuccess) return -3;
+      ++*launches;
+    }
+    return 0;
+  }
+  if (V) {
+    if (fill_identity(s, V, ncols) != cudaSuccess) return -3;
+    ++*launches;
+  }
+  const int npad = ncols + (ncols & 1);
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, kJacobiThreads, 0);
+  if (per_sm < 1) return -3;
+  int grid = npad / 2;
+  if (grid > nsm * per_sm) grid = nsm * per_sm;
+  if (cudaMemsetAsync(flags, 0, kDevFlagsResetBytes, s) != cudaSuccess) return -3;
+  const double tol = 2.220446049250313e-16 * std::sqrt((double)(nrows > 1 ? nrows : 1));
+  void* args[] = {&X, &nrows, &ncols, (void*)&npad, &V, &flags, &max_sweeps, (void*)&tol};
+  if (cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(grid), dim3(kJacobiThreads), args,
+                                  0, s) != cudaSuccess)
+    return -3;
+  ++*launches;
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// Norms, sorting, gathering
+// ---------------------------------------------------------------------------
+__global__ void colnorm_kernel(const double* __restrict__ X, int nrows, int ncols,
+                               double* __restrict__ sig) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  if (warp >= ncols) return;
+  const double* x = X + (long long)warp * nrows;
+  double acc = 0.0;
+  for (int r = lane; r < nrows; r += 32) acc = fma(x[r], x[r], acc);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) sig[warp] = sqrt(acc);
+}
+
+__global__ void rank_kernel(const double* __restrict__ sig, int n, int* __restrict__ perm) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const double sj = sig[j];
+    int rank = 0;
+    for (int i = 0; i < n; ++i) {
+      const double si = sig[i];
+      rank += (si > sj) || (si == sj && i < j);
+    }
+    perm[rank] = j;
+  }
+}
+
+cudaError_t column_norms_sorted(cudaStream_t s, const double* X, int nrows, int ncols, double* sig,
+                                int* perm) {
+  const int warps_per_block = 8;
+  colnorm_kernel<<<(ncols + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, s>>>(
+      X, nrows, ncols, sig);
+  rank_kernel<<<(ncols + 255) / 256, 256, 0, s>>>(sig, ncols, perm);
+  return cudaGetLastError();
+}
+
+__global__ void gather_cols_kernel(double* __restrict__ U, int rows, int k,
+                                   const double* __restrict__ X, const double* __restrict__ V,
+                                   const double* __restrict__ sig, const int* __restrict__ perm) {
+  const int r = blockIdx.x;
+  const int c = perm[r];
+  __shared__ double best_v[256];
+  __shared__ int best_i[256];
+  const double inv = V ? 1.0 : (sig[c] > 0.0 ? 1.0 / sig[c] : 0.0);
+  const double* src = V ? V + (long long)c * rows : X + (long long)c * rows;
+  double bv = -1.0;
+  int bi = 0x7fffffff;
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+    const double v = src[i] * inv;
+    U[(long long)i * k + r] = v;
+    if (fabs(v) > bv) {
+      bv = fabs(v);
+      bi = i;
+    }
+  }
+  best_v[threadIdx.x] = bv;
+  best_i[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double ov = best_v[threadIdx.x + o];
+      const int oi = best_i[threadIdx.x + o];
+      if (ov > best_v[threadIdx.x] || (ov == best_v[threadIdx.x] && oi < best_i[threadIdx.x])) {
+        best_v[threadIdx.x] = ov;
+        best_i[threadIdx.x] = oi;
+      }
+    }
+    __syncthreads();
+  }
+  const int im = best_i[0];
+  const bool flip = im < rows && U[(long long)im * k + r] < 0.0;
+  __syncthreads();
+  if (flip)
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) U[(long long)i * k + r] = -U[(long long)i * k + r];
+}
+
+cudaError_t gather_sorted_columns(cudaStream_t s, double* U, int rows, int k, const double* X,
+                                  const double* V, const double* sig, const int* perm) {
+  if (k <= 0) return cudaSuccess;
+  gather_cols_kernel<<<k, 256, 0, s>>>(U, rows, k, X, V, sig, perm);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Frobenius normalisation (deterministic two-level reduction)
+// ---------------------------------------------------------------------------
+constexpr int kNormBlocks = 304;
+
+__global__ void sumsq_partial_kernel(const double* __restrict__ x, long long n,
+                                     double* __restrict__ partial) {
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    acc = fma(x[i], x[i], acc);
+  double b = 0.0, c = 0.0;
+  block_sum3<256>(acc, b, c);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void scale_by_norm_kernel(double* __restrict__ x, long long n,
+                                     const double* __restrict__ partial, int nparts,
+                                     double* __restrict__ norm_out, int* __restrict__ bad) {
+  __shared__ double s_norm;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < nparts; ++i) t += partial[i];
+    s_norm = sqrt(t);
+  }
+  __syncthreads();
+  const double nrm = s_norm;
+  if (!(nrm > 0.0) || !isfinite(nrm)) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(bad, 1);
+    return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && norm_out) *norm_out = nrm;
+  const double inv = 1.0 / nrm;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    x[i] *= inv;
+}
+
+cudaError_t normalize_f64(cudaStream_t s, double* x, long long n, double* scratch, int* bad) {
+  // scratch: kNormBlocks + 1 doubles (partials, then the norm)
+  sumsq_partial_kernel<<<kNormBlocks, 256, 0, s>>>(x, n, scratch);
+  scale_by_norm_kernel<<<kNormBlocks, 256, 0, s>>>(x, n, scratch, kNormBlocks,
+                                                   scratch + kNormBlocks, bad);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Counter-based Gaussian fill
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void gaussian_kernel(double* __restrict__ x, long long n, unsigned long long seed) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long base = seed * 0xD1B54A32D192ED03ull + 2ull * (unsigned long long)i;
+    const unsigned long long z1 = splitmix64(base), z2 = splitmix64(base + 1ull);
+    const double u1 = ((double)(z1 >> 11) + 1.0) * 0x1.0p-53;  // (0, 1]
+    const double u2 = (double)(z2 >> 11) * 0x1.0p-53;          // [0, 1)
+    x[i] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+  }
+}
+
+cudaError_t gaussian_fill(cudaStream_t s, double* x, long long n, unsigned long long seed) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  gaussian_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, n, seed);
+  return cudaGetLastError();
+}
+
+}  // namespace ctm

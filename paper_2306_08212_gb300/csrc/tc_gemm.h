@@ -1,0 +1,21 @@
+// Tensor-core (tcgen05) contraction path for the TF32 / BF16 modes.
+#pragma once
+#include "ctm_internal.h"
+
+namespace ctm {
+
+struct TcGemm;
+
+// Returns nullptr when the tensor-core path cannot be set up.
+TcGemm* tc_create();
+void tc_destroy(TcGemm* t);
+
+// C(m, n) = sum_k A(m, k) B(k, n) with FP64 operands addressed through LegMaps
+// and an FP64 result, computed with TF32 (precision 1) or BF16 (precision 2)
+// products and FP32 accumulation.  Returns 0 on success.
+int tc_contract(TcGemm* t, cudaStream_t s, int precision, long long M, long long N, long long K,
+                const double* A, const LegMap& Am, const LegMap& Ak, const double* B,
+                const LegMap& Bk, const LegMap& Bn, double* C, const LegMap& Cm,
+                const LegMap& Cn, long long* launches);
+
+}  // namespace ctm

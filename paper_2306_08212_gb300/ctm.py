@@ -1,0 +1,244 @@
+"""ctypes binding of libctm (argument marshalling only; every step runs in the
+library's CUDA kernels).
+
+Module-level functions carry the C names (``ctm_init_env``, ``ctm_move``, ...)
+and return the C status; ``Env`` wraps a context and raises ``CtmError`` on a
+non-zero status.  Site tensors are real ``[d, D, D, D, D]`` arrays with legs
+(p, u, l, d, r), as numpy arrays (host) or CUDA torch tensors (device).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libctm.so")
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NAN, ERR_NOCONV, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+LEFT, UP, RIGHT, DOWN = 0, 1, 2, 3
+STANDARD, REDUCED_SEQUENTIAL = 0, 1
+FP64, TF32, BF16 = 0, 1, 2
+DIRS = {"left": LEFT, "up": UP, "right": RIGHT, "down": DOWN}
+MODES = {"standard": STANDARD, "reduced_sequential": REDUCED_SEQUENTIAL}
+PRECISIONS = {"fp64": FP64, "tf32": TF32, "bf16": BF16}
+
+_lib = None
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+
+SIGNATURES = {
+    "ctm_init_env": (ctypes.c_int, [ctypes.POINTER(_P), _P, _P, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P]),
+    "ctm_move": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "ctm_converge": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _I, _D]),
+    "ctm_expect_bond": (ctypes.c_int, [_P, ctypes.c_int, _D, _D]),
+    "ctm_corner_spectrum": (ctypes.c_int, [_P, ctypes.c_int, _D, _I]),
+    "ctm_log_kappa": (ctypes.c_int, [_P, _D]),
+    "ctm_get_tensor": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _I]),
+    "ctm_set_tensor": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _I]),
+    "ctm_kernel_launches": (ctypes.c_longlong, [_P]),
+    "ctm_last_error": (ctypes.c_char_p, [_P]),
+    "ctm_free": (None, [_P]),
+}
+
+
+class CtmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libctm error {code}: {msg}")
+        self.code = code
+
+
+def load(path=None):
+    """Load libctm.so (built by ``paper_2306_08212_gb300.build``); raises if missing."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise FileNotFoundError(f"{p} is missing: build it with paper_2306_08212_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_D)
+
+
+def _ptr_of(t):
+    """Host numpy (C-contiguous float64) or CUDA torch tensor -> (void*, keepalive)."""
+    if hasattr(t, "data_ptr") and hasattr(t, "is_cuda") and t.is_cuda:
+        import torch
+        if t.dtype != torch.float64 or not t.is_contiguous():
+            t = t.to(torch.float64).contiguous()
+        return ctypes.c_void_p(t.data_ptr()), t
+    a = np.ascontiguousarray(np.asarray(t, dtype=np.float64))
+    return ctypes.c_void_p(a.ctypes.data), a
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(0)
+
+
+# --- thin C-named wrappers -------------------------------------------------
+def ctm_init_env(A, B, chi, chi_prime=0, precision=FP64, boundary=None, stream=None):
+    """Returns (status, ctx_handle)."""
+    lib = load()
+    pa, ka = _ptr_of(A)
+    pb, kb = _ptr_of(B)
+    shape = tuple(A.shape)
+    d, D = int(shape[0]), int(shape[1])
+    pbnd, kbnd = (_ptr_of(boundary) if boundary is not None else (ctypes.c_void_p(0), None))
+    ctx = ctypes.c_void_p()
+    st = stream if stream is not None else _current_stream()
+    rc = lib.ctm_init_env(ctypes.byref(ctx), pa, pb, d, D, int(chi), int(chi_prime),
+                          int(precision), pbnd, st)
+    del ka, kb, kbnd
+    return rc, ctx
+
+
+def ctm_move(ctx, direction, mode):
+    return load().ctm_move(ctx, int(direction), int(mode))
+
+
+def ctm_converge(ctx, mode, max_iter, tol):
+    it = ctypes.c_int(0)
+    dl = ctypes.c_double(0.0)
+    rc = load().ctm_converge(ctx, int(mode), int(max_iter), float(tol), ctypes.byref(it),
+                             ctypes.byref(dl))
+    return rc, it.value, dl.value
+
+
+def ctm_expect_bond(ctx, bond, op):
+    op = np.ascontiguousarray(op, dtype=np.float64)
+    v = ctypes.c_double(0.0)
+    rc = load().ctm_expect_bond(ctx, int(bond), _dptr(op), ctypes.byref(v))
+    return rc, v.value
+
+
+def ctm_corner_spectrum(ctx, corner, maxlen):
+    s = np.zeros(maxlen)
+    n = ctypes.c_int(0)
+    rc = load().ctm_corner_spectrum(ctx, int(corner), _dptr(s), ctypes.byref(n))
+    return rc, s[: n.value]
+
+
+def ctm_log_kappa(ctx):
+    v = ctypes.c_double(0.0)
+    rc = load().ctm_log_kappa(ctx, ctypes.byref(v))
+    return rc, v.value
+
+
+def ctm_get_tensor(ctx, kind, k, x):
+    lib = load()
+    dims = (ctypes.c_int * 4)()
+    rc = lib.ctm_get_tensor(ctx, kind, k, x, None, dims)
+    if rc != OK:
+        return rc, None
+    shape = [v for v in dims if v > 0]
+    out = np.zeros(shape)
+    rc = lib.ctm_get_tensor(ctx, kind, k, x, _dptr(out), dims)
+    return rc, out
+
+
+def ctm_set_tensor(ctx, kind, k, x, arr):
+    arr = np.ascontiguousarray(arr, dtype=np.float64)
+    dims = (ctypes.c_int * 4)(*(list(arr.shape) + [0] * (4 - arr.ndim)))
+    return load().ctm_set_tensor(ctx, kind, k, x, _dptr(arr), dims)
+
+
+def ctm_kernel_launches(ctx):
+    return load().ctm_kernel_launches(ctx)
+
+
+def ctm_last_error(ctx):
+    return load().ctm_last_error(ctx).decode()
+
+
+def ctm_free(ctx):
+    load().ctm_free(ctx)
+
+
+# --- convenience wrapper -----------------------------------------------------
+class Env:
+    """A libctm context: the 16 environment tensors of a 2-site iPEPS on the GPU."""
+
+    def __init__(self, A, B, chi, chi_prime=0, precision="fp64", boundary=None, stream=None):
+        prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        self.chi = int(chi)
+        self.ctx = None
+        rc, ctx = ctm_init_env(A, B, chi, chi_prime, prec, boundary, stream)
+        if rc != OK:
+            msg = ctm_last_error(ctx) if ctx else "init failed"
+            raise CtmError(rc, msg)
+        self.ctx = ctx
+
+    def _check(self, rc):
+        if rc != OK:
+            raise CtmError(rc, ctm_last_error(self.ctx))
+
+    def move(self, direction, mode="reduced_sequential"):
+        d = DIRS[direction] if isinstance(direction, str) else int(direction)
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        self._check(ctm_move(self.ctx, d, m))
+
+    def converge(self, mode="reduced_sequential", max_iter=50, tol=1e-10, allow_noconv=True):
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        rc, it, dl = ctm_converge(self.ctx, m, max_iter, tol)
+        if not (rc == OK or (allow_noconv and rc == ERR_NOCONV)):
+            self._check(rc)
+        return it, dl
+
+    def expect_bond(self, bond, op):
+        rc, v = ctm_expect_bond(self.ctx, bond, op)
+        self._check(rc)
+        return v
+
+    def corner_spectrum(self, corner):
+        rc, s = ctm_corner_spectrum(self.ctx, corner, max(self.chi, 1) * 4 + 16)
+        self._check(rc)
+        return s
+
+    def corner_spectra(self):
+        return [self.corner_spectrum(i) for i in range(8)]
+
+    def log_kappa(self):
+        rc, v = ctm_log_kappa(self.ctx)
+        self._check(rc)
+        return v
+
+    def tensor(self, kind, k, x):
+        rc, t = ctm_get_tensor(self.ctx, kind, k, x)
+        self._check(rc)
+        return t
+
+    def set_tensor(self, kind, k, x, arr):
+        self._check(ctm_set_tensor(self.ctx, kind, k, x, arr))
+
+    @property
+    def launches(self):
+        return ctm_kernel_launches(self.ctx)
+
+    def free(self):
+        if self.ctx:
+            ctm_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
