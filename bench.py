@@ -1,0 +1,371 @@
+"""Benchmark: CTM moves/s of the reduced-sequential move at D=8, chi=256, d=2.
+
+One step = one CTM iteration: left, up, right and down moves (two column
+absorptions each: reduced network, split isometries, sequential absorption,
+normalisation) plus the FP64 convergence check (singular values of the 8
+corners).  value = 4 * steps / device time (moves/s, whole job over N GPUs).
+
+Inputs: A, B with i.i.d. N(0,1) entries, unit Frobenius norm (seeds 0, 1),
+environment folded and grown to chi on the device before timing.  The working
+set (16 environment tensors of up to chi*D*D*chi doubles, ~0.5 GB, plus GB of
+intermediates) is larger than the 129 MB L2, so no flush is needed between
+steps.
+
+--impl reference times the CPU oracle (plain NumPy/LAPACK FP64) on a bounded
+sample of the same workload (one reduced-sequential column absorption at the
+same shapes) and scales it to moves/s.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+D_, CHI, PHYS = 8, 256, 2
+WORKLOAD = "iPEPS 2-site {A,B} CTM iteration, d=2 D=8 chi=256 chi'=256, reduced-sequential"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="native", choices=["native", "reference"])
+    p.add_argument("--precision", default=os.environ.get("CTM_BENCH_PRECISION", "bf16"))
+    p.add_argument("--D", type=int, default=D_)
+    p.add_argument("--chi", type=int, default=CHI)
+    p.add_argument("--no-standard", action="store_true",
+                   help="skip timing one FP64 standard move for comparison")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (one process per GPU; independent replicas)
+# ---------------------------------------------------------------------------
+def dist_setup(n):
+    import torch
+    if n <= 1 or "RANK" not in os.environ:
+        return 0, 1, None
+    import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl")
+    return dist.get_rank(), dist.get_world_size(), dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, v):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def fp64_gemm_peak():
+    """cuBLAS DGEMM throughput on this GPU (TFLOP/s), the FP64 ALU denominator."""
+    import torch
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        a @ b
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = 1e30
+    for _ in range(3):
+        e0.record()
+        a @ b
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3)
+    return 2.0 * n ** 3 / best / 1e12
+
+
+def run_native(args):
+    import numpy as np
+    import torch
+
+    from paper_2306_08212_gb300 import ctm, inputs
+
+    rank, world, dist = dist_setup(args.gpus)
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ctm.load()
+    stream = torch.cuda.current_stream()
+    A, B = inputs.random_sites(PHYS, args.D, 0)
+    env = ctm.Env(A, B, args.chi, precision=args.precision)
+    ctx = env.ctx
+    order = (ctm.LEFT, ctm.UP, ctm.RIGHT, ctm.DOWN)
+
+    def step():
+        for d in order:
+            rc = ctm.ctm_move(ctx, d, ctm.REDUCED_SEQUENTIAL)
+            if rc != ctm.OK:
+                raise RuntimeError(ctm.ctm_last_error(ctx))
+        for corner in range(8):  # convergence check: FP64 corner spectra
+            rc, _ = ctm.ctm_corner_spectrum(ctx, corner, args.chi + 16)
+            if rc != ctm.OK:
+                raise RuntimeError(ctm.ctm_last_error(ctx))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctm.ctm_kernel_stats_reset(ctx)
+    launches0 = ctm.ctm_kernel_launches(ctx)
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    barrier(dist)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(dist)
+    clk = clocks.stop()
+    t = e0.elapsed_time(e1) / 1e3
+    t = max_over_ranks(dist, t)
+    launches = ctm.ctm_kernel_launches(ctx) - launches0
+    stats = ctm.ctm_kernel_stats(ctx)
+
+    # end to end through the C ABI with host buffers: environment in (pinned
+    # host -> device), one iteration, the 8 corner spectra out (device -> host)
+    host_env = {}
+    for kind in (0, 1):
+        for k in range(1, 5):
+            for x in (0, 1):
+                t_np = env.tensor(kind, k, x)
+                host_env[(kind, k, x)] = torch.from_numpy(t_np).pin_memory()
+    h2d = sum(v.numel() * 8 for v in host_env.values())
+    d2h = 8 * (args.chi + 0) * 8
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for (kind, k, x), v in host_env.items():
+            dims = (ctm.ctypes.c_int * 4)(*(list(v.shape) + [0] * (4 - v.dim())))
+            rc = ctm.load().ctm_set_tensor(ctx, kind, k, x,
+                                           ctm.ctypes.cast(v.data_ptr(), ctm._D), dims)
+            assert rc == ctm.OK, ctm.ctm_last_error(ctx)
+        step()
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(dist, time.perf_counter() - t0)
+
+    std = None
+    if not args.no_standard and rank == 0:
+        std = time_standard(args, A, B)
+
+    if rank != 0:
+        env.free()
+        return None
+    peaks, peaks_kind = measured_peaks()
+    moves = 4 * args.steps * world
+    value = moves / t
+    roof = roofline(args, stats, peaks, peaks_kind)
+    line = {
+        "metric": "CTM moves/s at D=8 chi=256 (reduced-sequential, mixed precision)",
+        "value": value,
+        "unit": "moves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"fp64": "f64", "tf32": "tf32/f32acc+f64", "bf16": "bf16/f32acc+f64"}[args.precision],
+        "data": "synthetic: A,B ~ N(0,1) unit norm, seeds 0/1",
+        "config": {"workload": WORKLOAD.replace("D=8", f"D={args.D}").replace("chi=256", f"chi={args.chi}"),
+                   "precision": args.precision, "parallelism": f"replicas{world}",
+                   "l2": "working set > L2 (no flush)"},
+        "e2e": {"value": moves / t_e2e, "unit": "moves/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "roofline": roof,
+    }
+    if std is not None:
+        line["fp64_standard"] = std
+        line["speedup_vs_fp64_standard"] = value / std["value"]
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args)
+    env.free()
+    return line
+
+
+def time_standard(args, A, B):
+    """One FP64 standard move (Sec. II, O(chi^3 D^6)) on the same grown environment."""
+    import torch
+
+    from paper_2306_08212_gb300 import ctm
+    env = ctm.Env(A, B, args.chi, precision="fp64")
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    env.move("left", "standard")
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    env.free()
+    return {"value": 1.0 / t, "unit": "moves/s", "moves_timed": 1, "dtype": "f64"}
+
+
+def roofline(args, stats, peaks, peaks_kind):
+    if not stats:
+        return None
+    top = max(stats, key=lambda s: s["ms"])
+    if top["count"] == 0 or top["ms"] <= 0:
+        return None
+    avg_s = top["ms"] / top["count"] / 1e3
+    flops_per_launch = top["flops"] / top["count"]
+    achieved = flops_per_launch / avg_s / 1e12
+    if top["name"].startswith("tc_bf16"):
+        peak, bound, note = peaks["bf16_tflops_sustained"], "tensor", f"bf16 sustained ({peaks_kind})"
+    elif top["name"].startswith("tc_tf32"):
+        peak = peaks["bf16_tflops_sustained"] * (1.1 / 2.25)
+        bound, note = "tensor", f"tf32 = bf16 sustained ({peaks_kind}) x 1.1/2.25"
+    else:
+        peak, bound, note = fp64_gemm_peak(), "alu", "fp64: cuBLAS DGEMM measured here"
+    return {"kernel": top["name"], "bound": bound, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "launches": top["count"], "avg_launch_us": avg_s * 1e6, "peak_source": note}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_column_seconds(D, chi):
+    """Seconds for one reduced-sequential column absorption of the oracle at (D, chi)."""
+    import numpy as np
+
+    from oracle import ctm_oracle as O
+    from paper_2306_08212_gb300 import inputs
+    A, B = inputs.random_sites(PHYS, D, 0)
+    env = inputs.random_env_tensors(D, chi, seed=2)
+    sites = {"a": A, "b": B}
+    t0 = time.perf_counter()
+    O.column_absorb(env, 0, sites, chi, chi, "reduced_sequential")
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(args):
+    sec = oracle_column_seconds(args.D, args.chi)
+    return {"value": 1.0 / (2.0 * sec), "unit": "moves/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"one reduced-sequential column absorption (half a move) at D={args.D} "
+                      f"chi={args.chi} on a seeded random environment, x2 per move"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    times = []
+    for _ in range(args.warmup):
+        oracle_column_seconds(args.D, args.chi)
+    for _ in range(args.steps):
+        times.append(oracle_column_seconds(args.D, args.chi))
+    t = sum(times)
+    # one step = 4 moves = 8 column absorptions; the sample times one column each
+    value = len(times) / (2.0 * t)
+    cb = {"value": value, "unit": "moves/s", "cores": os.cpu_count(), "kind": "oracle",
+          "sample": "one reduced-sequential column absorption per step at the bench shapes"}
+    return {"impl": "reference", "metric": "CTM moves/s at D=8 chi=256 (reduced-sequential, mixed precision)",
+            "value": value, "unit": "moves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
+            "config": {"workload": WORKLOAD}, "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "moves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        line = run_reference(args)
+    else:
+        line = run_native(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -129,6 +129,18 @@ int ctm_set_tensor(ctm_ctx* ctx, int kind, int k, int x, const double* in,
 /* Number of kernels this library launched on the context so far. */
 long long ctm_kernel_launches(ctm_ctx* ctx);
 
+/*
+ * Per-class kernel timing with CUDA events recorded on the context's stream
+ * around every launch of a class (0 = FP64 contraction, 1 = TF32 tensor-core
+ * contraction, 2 = BF16 tensor-core contraction, 3 = Jacobi SVD sweep kernel).
+ * ctm_profile_enable(ctx, 1) clears the counters and starts recording; 0 stops.
+ * ctm_profile_read synchronises the stream and returns, for one class, the
+ * launches, their summed device time in ms and their algorithmic flop count
+ * (2 M N K for a contraction, 0 for Jacobi whose work depends on the data).
+ */
+int ctm_profile_enable(ctm_ctx* ctx, int on);
+int ctm_profile_read(ctm_ctx* ctx, int cls, long long* launches, double* ms, double* flops);
+
 /* Message of the last failure on ctx ("" if none); valid until the next call. */
 const char* ctm_last_error(ctm_ctx* ctx);
 

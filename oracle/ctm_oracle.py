@@ -48,8 +48,9 @@ import functools
 
 import numpy as np
 
-# every contraction goes through BLAS-backed einsum (pairwise tensordot); the
-# multi-operand ones only name a network whose value is order-independent
+# every contraction is pairwise (two operands) and goes through BLAS-backed
+# einsum; multi-operand calls are avoided because numpy's path search can pick
+# outer products far larger than any tensor of the method
 ein = functools.partial(np.einsum, optimize=True)
 
 OTHER = {"a": "b", "b": "a"}
@@ -105,14 +106,17 @@ class View:
 def _fold_C1(A, bnd):
     """Corner C1[down, right] of site A with its up and left legs closed by bnd."""
     D = A.shape[1]
-    C = ein("puldr,pULDR,uU,lL->dDrR", A, A.conj(), bnd, bnd)
+    X = ein("puldr,uU->pUldr", A, bnd)
+    X = ein("pUldr,lL->pULdr", X, bnd)
+    C = ein("pULdr,pULDR->dDrR", X, A.conj())
     return C.reshape(D * D, D * D)
 
 
 def _fold_T1(A, bnd):
     """Edge T1[down, k, b, up] of site A with its left leg closed by bnd."""
     D = A.shape[1]
-    T = ein("puldr,pULDR,lL->dDrRuU", A, A.conj(), bnd)
+    X = ein("puldr,lL->puLdr", A, bnd)
+    T = ein("puLdr,pULDR->dDrRuU", X, A.conj())
     return T.reshape(D * D, D, D, D * D)
 
 
@@ -245,8 +249,12 @@ def projector_standard(V, x, sites, chi):
     T2xf = T2x.reshape(T2x.shape[0], D * D, T2x.shape[3])
     T2yf = T2y.reshape(T2y.shape[0], D * D, T2y.shape[3])
     T3f = T3.reshape(T3.shape[0], D * D, T3.shape[3])
-    EL = ein("dg,gUe,aLd,ULXR->aXeR", C1, T2xf, T1f, ax)
-    ER = ein("eUz,zh,hRb,ULYR->eLbY", T2yf, C2, T3f, ay)
+    EL = ein("dg,gUe->dUe", C1, T2xf)
+    EL = ein("dUe,aLd->aLUe", EL, T1f)
+    EL = ein("aLUe,ULXR->aXeR", EL, ax)
+    ER = ein("eUz,zh->eUh", T2yf, C2)
+    ER = ein("eUh,hRb->eURb", ER, T3f)
+    ER = ein("eURb,ULYR->eLbY", ER, ay)
     Q = ein("aXeR,eRbY->aXYb", EL, ER)
     na = Q.shape[0]
     Qm = Q.reshape(na * D * D, -1)
@@ -285,10 +293,10 @@ def reduced_network(V, x, sites, chi, chip):
     R = ein("ez,zkbw->ekbw", C2, T3)       # [C2.left, k, b, T3.down]
     vl1, vl2 = split_projector(L, chi, chip)
     vr1, vr2 = split_projector(R, chi, chip)
-    C1p = ein("gkc,cby,gkba->ya", vl1, vl2, L)
-    C2p = ein("ekc,cby,ekbw->yw", vr1, vr2, R)
+    C1p = ein("cby,cba->ya", vl2, ein("gkc,gkba->cba", vl1, L))
+    C2p = ein("cby,cbw->yw", vr2, ein("ekc,ekbw->cbw", vr1, R))
     T2p = absorb_edge_seq(T2, edge_site_T2(sites[x]), vl1, vl2, vr1, vr2)
-    return ein("ya,ykbz,zw->akbw", C1p, T2p, C2p)
+    return ein("akbz,zw->akbw", ein("ya,ykbz->akbz", C1p, T2p), C2p)
 
 
 def projector_reduced_seq(V, x, sites, chi, chip):
@@ -440,8 +448,16 @@ def bond_rdm(env, A, B, r, x):
     T3, C3, T4y, T4x = f(V("T", 3, y)), V("C", 3, y), f(V("T", 4, y)), f(V("T", 4, x))
     C4, T1 = V("C", 4, x), f(V("T", 1, x))
     ax, ay = _open_double(site[x]), _open_double(site[y])
-    left = ein("dg,gUe,mLd,lm,kXl,pPULXR->eRkpP", C1, T2x, T1, C4, T4x, ax)
-    right = ein("eVz,zh,hWt,ti,iYk,qQVRYW->eRkqQ", T2y, C2, T3, C3, T4y, ay)
+    left = ein("dg,gUe->dUe", C1, T2x)
+    left = ein("dUe,mLd->mLUe", left, T1)
+    left = ein("mLUe,lm->lLUe", left, C4)
+    left = ein("lLUe,kXl->kXLUe", left, T4x)
+    left = ein("kXLUe,pPULXR->eRkpP", left, ax)
+    right = ein("eVz,zh->eVh", T2y, C2)
+    right = ein("eVh,hWt->eVWt", right, T3)
+    right = ein("eVWt,ti->eVWi", right, C3)
+    right = ein("eVWi,iYk->eVWYk", right, T4y)
+    right = ein("eVWYk,qQVRYW->eRkqQ", right, ay)
     rho = ein("eRkpP,eRkqQ->pqPQ", left, right)
     return rho.reshape(d * d, d * d)
 
@@ -466,7 +482,16 @@ def heisenberg_bond():
 
 
 def _trace_net(tensors, spec):
-    return float(ein(spec, *tensors))
+    """Close a ring of tensors pairwise, left to right, in the order given."""
+    ins, _ = spec.split("->")
+    labels = ins.split(",")
+    acc, acc_l = tensors[0], labels[0]
+    for t, lab in zip(tensors[1:], labels[1:]):
+        keep = [ch for ch in acc_l + lab if (acc_l + lab).count(ch) == 1]
+        out = "".join(keep)
+        acc = ein(f"{acc_l},{lab}->{out}", acc, t)
+        acc_l = out
+    return float(acc)
 
 
 def _log_kappa_from(V, x, y):

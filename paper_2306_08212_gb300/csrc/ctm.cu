@@ -55,6 +55,14 @@ struct ctm_ctx {
   std::string err;
   std::vector<void*> owned;  // long-lived device allocations
   TcGemm* tc = nullptr;      // tensor-core GEMM state (mixed precision)
+  struct ProfClass {
+    std::vector<cudaEvent_t> ev;  // pairs (start, stop)
+    size_t used = 0;
+    long long count = 0;
+    double ms = 0.0, flops = 0.0;
+  };
+  bool prof_on = false;
+  ProfClass prof[4];
 };
 
 namespace {
@@ -134,6 +142,47 @@ Ten view(const Ten& t, std::initializer_list<int> dims) {
   }
   if (s != t.size()) fail(CTM_ERR_ARG, "internal: reshape size mismatch");
   return v;
+}
+
+// ---------------------------------------------------------------------------
+// Optional per-class kernel timing (CUDA events on the context's stream)
+// ---------------------------------------------------------------------------
+struct ProfScope {
+  ctm_ctx* c;
+  int cls;
+  size_t slot = 0;
+  bool on;
+  ProfScope(ctm_ctx* ctx, int k, double flops) : c(ctx), cls(k), on(ctx->prof_on) {
+    if (!on) return;
+    auto& pc = c->prof[cls];
+    if (pc.used + 2 > pc.ev.size()) {
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) fail(CTM_ERR_CUDA, "event create");
+        pc.ev.push_back(e);
+      }
+    }
+    slot = pc.used;
+    pc.used += 2;
+    pc.count += 1;
+    pc.flops += flops;
+    cudaEventRecord(pc.ev[slot], c->stream);
+  }
+  ~ProfScope() {
+    if (on) cudaEventRecord(c->prof[cls].ev[slot + 1], c->stream);
+  }
+};
+
+void prof_collect(ctm_ctx* c) {
+  cudaStreamSynchronize(c->stream);
+  for (auto& pc : c->prof) {
+    for (size_t i = 0; i + 1 < pc.used; i += 2) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pc.ev[i], pc.ev[i + 1]) == cudaSuccess) pc.ms += ms;
+    }
+    pc.used = 0;
+  }
+  cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -263,9 +312,12 @@ Plan make_plan(const Spec& s, const Ten& A, const Ten& B) {
 Tmp ein64(ctm_ctx* c, const char* spec, const Ten& A, const Ten& B) {
   Plan p = make_plan(parse(spec), A, B);
   Tmp C(c, p.out_dims, p.out_nd);
-  ck(gemm_f64(c->stream, p.M, p.N, p.K, 1.0, A.p, p.Am, p.Ak, B.p, p.Bk, p.Bn, 0.0, C.t.p, p.Cm,
-              p.Cn),
-     spec);
+  {
+    ProfScope ps(c, 0, 2.0 * p.M * p.N * p.K);
+    ck(gemm_f64(c->stream, p.M, p.N, p.K, 1.0, A.p, p.Am, p.Ak, B.p, p.Bk, p.Bn, 0.0, C.t.p,
+                p.Cm, p.Cn),
+       spec);
+  }
   ++c->launches;
   return C;
 }
@@ -275,6 +327,7 @@ Tmp ein(ctm_ctx* c, const char* spec, const Ten& A, const Ten& B) {
   if (c->precision == CTM_FP64) return ein64(c, spec, A, B);
   Plan p = make_plan(parse(spec), A, B);
   Tmp C(c, p.out_dims, p.out_nd);
+  ProfScope ps(c, c->precision == CTM_TF32 ? 1 : 2, 2.0 * p.M * p.N * p.K);
   int rc = tc_contract(c->tc, c->stream, c->precision, p.M, p.N, p.K, A.p, p.Am, p.Ak, B.p,
                        p.Bk, p.Bn, C.t.p, p.Cm, p.Cn, &c->launches);
   if (rc != 0) fail(CTM_ERR_CUDA, std::string("tensor-core contraction failed: ") + spec);
@@ -285,6 +338,7 @@ Tmp ein(ctm_ctx* c, const char* spec, const Ten& A, const Ten& B) {
 // Factorisations (FP64)
 // ---------------------------------------------------------------------------
 void jacobi(ctm_ctx* c, double* X, int nrows, int ncols, double* V) {
+  ProfScope ps(c, 3, 0.0);
   int rc = jacobi_onesided(c->stream, X, nrows, ncols, V, c->flags, kMaxSweeps, &c->launches);
   if (rc != 0) fail(CTM_ERR_CUDA, "Jacobi launch failed");
 }
@@ -395,8 +449,11 @@ Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k) {
     push(Bn, l, 1);
     push(Cm, rows, 1);
     push(Cn, l, rows);
-    ck(gemm_f64(c->stream, rows, l, cols, 1.0, M, Mrow, Mcol, Rrow, Bk, Bn, 0.0, Y.t.p, Cm, Cn),
-       "M Q");
+    {
+      ProfScope ps(c, 0, 2.0 * rows * l * cols);
+      ck(gemm_f64(c->stream, rows, l, cols, 1.0, M, Mrow, Mcol, Rrow, Bk, Bn, 0.0, Y.t.p, Cm, Cn),
+         "M Q");
+    }
     ++c->launches;
     return Y;
   };
@@ -410,8 +467,11 @@ Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k) {
     push(Bn, l, 1);
     push(Cm, cols, 1);
     push(Cn, l, cols);
-    ck(gemm_f64(c->stream, cols, l, rows, 1.0, M, Am, Ak, Qrow, Bk, Bn, 0.0, Z.t.p, Cm, Cn),
-       "M^T Q");
+    {
+      ProfScope ps(c, 0, 2.0 * rows * l * cols);
+      ck(gemm_f64(c->stream, cols, l, rows, 1.0, M, Am, Ak, Qrow, Bk, Bn, 0.0, Z.t.p, Cm, Cn),
+         "M^T Q");
+    }
     ++c->launches;
     return Z;
   };
@@ -1077,6 +1137,28 @@ int ctm_set_tensor(ctm_ctx* c, int kind, int k, int x, const double* in, const i
 
 long long ctm_kernel_launches(ctm_ctx* c) { return c ? c->launches : 0; }
 
+int ctm_profile_enable(ctm_ctx* c, int on) {
+  if (!c) return CTM_ERR_ARG;
+  return guarded(c, [&] {
+    prof_collect(c);
+    for (auto& pc : c->prof) {
+      pc.count = 0;
+      pc.ms = pc.flops = 0.0;
+    }
+    c->prof_on = on != 0;
+  });
+}
+
+int ctm_profile_read(ctm_ctx* c, int cls, long long* launches, double* ms, double* flops) {
+  if (!c || cls < 0 || cls > 3 || !launches || !ms || !flops) return CTM_ERR_ARG;
+  return guarded(c, [&] {
+    prof_collect(c);
+    *launches = c->prof[cls].count;
+    *ms = c->prof[cls].ms;
+    *flops = c->prof[cls].flops;
+  });
+}
+
 const char* ctm_last_error(ctm_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 void ctm_free(ctm_ctx* c) {
@@ -1084,6 +1166,8 @@ void ctm_free(ctm_ctx* c) {
   cudaStreamSynchronize(c->stream);
   for (void* p : c->owned) cudaFree(p);
   if (c->tc) tc_destroy(c->tc);
+  for (auto& pc : c->prof)
+    for (cudaEvent_t e : pc.ev) cudaEventDestroy(e);
   cudaGetLastError();
   delete c;
 }

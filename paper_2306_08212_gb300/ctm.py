@@ -39,6 +39,8 @@ SIGNATURES = {
     "ctm_get_tensor": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _I]),
     "ctm_set_tensor": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _I]),
     "ctm_kernel_launches": (ctypes.c_longlong, [_P]),
+    "ctm_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ctm_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _D, _D]),
     "ctm_last_error": (ctypes.c_char_p, [_P]),
     "ctm_free": (None, [_P]),
 }
@@ -162,6 +164,39 @@ def ctm_set_tensor(ctx, kind, k, x, arr):
 
 def ctm_kernel_launches(ctx):
     return load().ctm_kernel_launches(ctx)
+
+
+PROFILE_CLASSES = {0: "gemm_f64", 1: "tc_tf32_gemm", 2: "tc_bf16_gemm", 3: "jacobi_f64"}
+
+
+def ctm_profile_enable(ctx, on=True):
+    return load().ctm_profile_enable(ctx, int(bool(on)))
+
+
+def ctm_profile_read(ctx, cls):
+    n = ctypes.c_longlong(0)
+    ms = ctypes.c_double(0.0)
+    fl = ctypes.c_double(0.0)
+    rc = load().ctm_profile_read(ctx, int(cls), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(fl))
+    return rc, n.value, ms.value, fl.value
+
+
+def ctm_kernel_stats_reset(ctx):
+    """Clear and start the per-class CUDA-event kernel timing."""
+    rc = ctm_profile_enable(ctx, True)
+    if rc != OK:
+        raise CtmError(rc, ctm_last_error(ctx))
+
+
+def ctm_kernel_stats(ctx):
+    """[{name, count, ms, flops}] per kernel class since the last reset."""
+    out = []
+    for cls, name in PROFILE_CLASSES.items():
+        rc, n, ms, fl = ctm_profile_read(ctx, cls)
+        if rc != OK:
+            raise CtmError(rc, ctm_last_error(ctx))
+        out.append({"name": name, "count": n, "ms": ms, "flops": fl})
+    return out
 
 
 def ctm_last_error(ctx):
