@@ -141,6 +141,24 @@ long long ctm_kernel_launches(ctm_ctx* ctx);
 int ctm_profile_enable(ctm_ctx* ctx, int on);
 int ctm_profile_read(ctm_ctx* ctx, int cls, long long* launches, double* ms, double* flops);
 
+/*
+ * Singular values of a device matrix M (row-major rows x cols, device pointer)
+ * into the device buffer s (min(rows, cols) doubles), descending and scaled to
+ * sum s^2 = 1 -- the same values ctm_corner_spectrum returns for a corner --
+ * without allocating any device memory.  (The paper has no counterpart: this
+ * serves callers that cannot allocate, e.g. inside a runtime that owns the
+ * device memory or forbids cudaMalloc/cudaFree after start-up.)
+ * Scratch: one fixed __device__ array inside the library (about 8.1 MB on every
+ * GPU that loads it, held until exit) whose device address is looked up during
+ * the first call on each device -- make that first call before any stream
+ * capture.  Limits: rows * cols <= 1048576 and min(rows, cols) <= 4096, else
+ * CTM_ERR_ARG.  All calls share the array: calls whose GPU work overlaps race
+ * and must be serialised.  The call synchronises `stream` (a cudaStream_t) to
+ * report CTM_ERR_NOCONV / CTM_ERR_CUDA.  M is not modified.
+ */
+int ctm_singular_values_noalloc(const double* M, int rows, int cols, double* s,
+                                void* stream);
+
 /* Message of the last failure on ctx ("" if none); valid until the next call. */
 const char* ctm_last_error(ctm_ctx* ctx);
 

@@ -41,6 +41,7 @@ SIGNATURES = {
     "ctm_kernel_launches": (ctypes.c_longlong, [_P]),
     "ctm_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "ctm_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _D, _D]),
+    "ctm_singular_values_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "ctm_last_error": (ctypes.c_char_p, [_P]),
     "ctm_free": (None, [_P]),
 }
@@ -197,6 +198,17 @@ def ctm_kernel_stats(ctx):
             raise CtmError(rc, ctm_last_error(ctx))
         out.append({"name": name, "count": n, "ms": ms, "flops": fl})
     return out
+
+
+def ctm_singular_values_noalloc(M_ptr, rows, cols, s_ptr, stream=None):
+    """Singular values of a device matrix into a device buffer, allocating nothing.
+
+    M_ptr / s_ptr are device addresses (e.g. ``tensor.data_ptr()``); for callers
+    that must not allocate device memory during the call.  Returns the status.
+    """
+    st = stream if stream is not None else _current_stream()
+    return load().ctm_singular_values_noalloc(ctypes.c_void_p(M_ptr), int(rows), int(cols),
+                                              ctypes.c_void_p(s_ptr), st)
 
 
 def ctm_last_error(ctx):
