@@ -159,6 +159,15 @@ int ctm_profile_read(ctm_ctx* ctx, int cls, long long* launches, double* ms, dou
 int ctm_singular_values_noalloc(const double* M, int rows, int cols, double* s,
                                 void* stream);
 
+/*
+ * Test hook for the contraction kernels: C = A B for host row-major A (M x K),
+ * B (K x N), C (M x N), computed on the current device in `precision`
+ * (CTM_FP64: the FP64 leg-map kernel; CTM_TF32 / CTM_BF16: the tcgen05 kernel
+ * with FP32 accumulation).  Allocates its own device buffers; synchronous.
+ */
+int ctm_contract_test(int precision, long long M, long long N, long long K, const double* A,
+                      const double* B, double* C);
+
 /* Message of the last failure on ctx ("" if none); valid until the next call. */
 const char* ctm_last_error(ctm_ctx* ctx);
 

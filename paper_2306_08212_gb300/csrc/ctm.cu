@@ -329,7 +329,7 @@ Tmp ein(ctm_ctx* c, const char* spec, const Ten& A, const Ten& B) {
   Tmp C(c, p.out_dims, p.out_nd);
   ProfScope ps(c, c->precision == CTM_TF32 ? 1 : 2, 2.0 * p.M * p.N * p.K);
   int rc = tc_contract(c->tc, c->stream, c->precision, p.M, p.N, p.K, A.p, p.Am, p.Ak, B.p,
-                       p.Bk, p.Bn, C.t.p, p.Cm, p.Cn, &c->launches);
+                       p.Bk, p.Bn, C.t.p, p.Cm, p.Cn, &c->launches, &c->flags->error);
   if (rc != 0) fail(CTM_ERR_CUDA, std::string("tensor-core contraction failed: ") + spec);
   return C;
 }
@@ -1136,6 +1136,72 @@ int ctm_set_tensor(ctm_ctx* c, int kind, int k, int x, const double* in, const i
 }
 
 long long ctm_kernel_launches(ctm_ctx* c) { return c ? c->launches : 0; }
+
+int ctm_contract_test(int precision, long long M, long long N, long long K, const double* A,
+                      const double* B, double* C) {
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !C) return CTM_ERR_ARG;
+  if (precision != CTM_FP64 && precision != CTM_TF32 && precision != CTM_BF16) return CTM_ERR_ARG;
+  double *dA = nullptr, *dB = nullptr, *dC = nullptr;
+  TcGemm* tc = nullptr;
+  int rc = CTM_OK;
+  long long launches = 0;
+  auto bail = [&](int code) {
+    rc = code;
+    return;
+  };
+  do {
+    if (cudaMalloc(&dA, sizeof(double) * M * K) != cudaSuccess ||
+        cudaMalloc(&dB, sizeof(double) * K * N) != cudaSuccess ||
+        cudaMalloc(&dC, sizeof(double) * M * N) != cudaSuccess) {
+      bail(CTM_ERR_OOM);
+      break;
+    }
+    cudaMemcpy(dA, A, sizeof(double) * M * K, cudaMemcpyHostToDevice);
+    cudaMemcpy(dB, B, sizeof(double) * K * N, cudaMemcpyHostToDevice);
+    cudaMemset(dC, 0, sizeof(double) * M * N);
+    LegMap Am, Ak, Bk, Bn, Cm, Cn;
+    Am.n = Ak.n = Bk.n = Bn.n = Cm.n = Cn.n = 1;
+    Am.dim[0] = Cm.dim[0] = (int)M;
+    Ak.dim[0] = Bk.dim[0] = (int)K;
+    Bn.dim[0] = Cn.dim[0] = (int)N;
+    Am.stride[0] = K;
+    Ak.stride[0] = 1;
+    Bk.stride[0] = N;
+    Bn.stride[0] = 1;
+    Cm.stride[0] = N;
+    Cn.stride[0] = 1;
+    if (precision == CTM_FP64) {
+      if (gemm_f64(0, M, N, K, 1.0, dA, Am, Ak, dB, Bk, Bn, 0.0, dC, Cm, Cn) != cudaSuccess) {
+        bail(CTM_ERR_CUDA);
+        break;
+      }
+    } else {
+      tc = tc_create();
+      if (!tc) {
+        bail(CTM_ERR_UNSUPPORTED);
+        break;
+      }
+      if (tc_contract(tc, 0, precision, M, N, K, dA, Am, Ak, dB, Bk, Bn, dC, Cm, Cn, &launches,
+                      nullptr) != 0) {
+        bail(CTM_ERR_CUDA);
+        break;
+      }
+      if (tc_error(tc, 0) != 0) {
+        bail(CTM_ERR_CUDA);
+        break;
+      }
+    }
+    if (cudaMemcpy(C, dC, sizeof(double) * M * N, cudaMemcpyDeviceToHost) != cudaSuccess)
+      bail(CTM_ERR_CUDA);
+  } while (false);
+  cudaDeviceSynchronize();
+  if (cudaGetLastError() != cudaSuccess && rc == CTM_OK) rc = CTM_ERR_CUDA;
+  cudaFree(dA);
+  cudaFree(dB);
+  cudaFree(dC);
+  tc_destroy(tc);
+  return rc;
+}
 
 int ctm_profile_enable(ctm_ctx* c, int on) {
   if (!c) return CTM_ERR_ARG;

@@ -1,20 +1,440 @@
-// Placeholder until the tcgen05 kernels land: the mixed-precision modes report
-// CTM_ERR_UNSUPPORTED instead of silently running in FP64.
+// Tensor-core contractions for the mixed-precision modes: operands gathered
+// through leg maps, cast to BF16 (or rounded to TF32) and packed K-major, then a
+// tcgen05 GEMM: TMA loads 128-byte-swizzled tiles into a multi-stage shared
+// memory ring (mbarrier pipeline), one thread issues tcgen05.mma into a TMEM
+// accumulator (FP32), and four warps read TMEM back with tcgen05.ld and write
+// the result through the output leg map.
+//
+// Every wait on an mbarrier has a time limit (about one second of
+// %globaltimer); on expiry the kernel records an error word, skips the rest of
+// its work, releases its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <cstdint>
+#include <mutex>
+
 #include "tc_gemm.h"
 
 namespace ctm {
 
+__device__ __forceinline__ long long tc_map_offset(const LegMap& m, long long idx) {
+  long long off = 0;
+  for (int l = m.n - 1; l >= 0; --l) {
+    const long long d = m.dim[l];
+    const long long q = idx / d;
+    off += (idx - q * d) * m.stride[l];
+    idx = q;
+  }
+  return off;
+}
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // one second
+
+// Bounded wait on an mbarrier phase; false on timeout or when another thread
+// already reported an error.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = globaltimer_ns();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*(volatile int*)err) return false;
+    if (globaltimer_ns() - t0 > kWaitLimitNs) {
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand tile of rows x 128 bytes
+// with the 128-byte swizzle (written so by TMA), 1024-byte aligned; 8-row
+// groups are 1024 bytes apart (stride byte offset); descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void* p) {
+  const uint64_t addr = smem_u32(p);
+  uint64_t d = (addr >> 4) & 0x3FFFull;         // start address
+  d |= (uint64_t)(16 >> 4) << 16;               // leading byte offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;             // stride byte offset
+  d |= (uint64_t)1 << 46;                       // descriptor version
+  d |= (uint64_t)2 << 61;                       // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: FP32 accumulator, A/B format (1 = BF16, 2 = TF32),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t make_idesc(int M, int N, uint32_t ab_fmt) {
+  return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+template <bool TF32>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                     uint32_t idesc, uint32_t accumulate) {
+  if constexpr (TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  }
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+// 32 lanes x 32 consecutive 32-bit TMEM columns into 32 registers per thread.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// GEMM kernel: C[128 x BN tile] = A_packed (M x Kp, K-major) . B_packed^T (N x Kp)
+// ---------------------------------------------------------------------------
+constexpr int kBM = 128;
+constexpr int kStageKBytes = 128;  // one swizzle atom of K per stage
+
+template <int BN>
+__host__ __device__ constexpr int tc_stages() {
+  return BN == 256 ? 4 : 6;
+}
+
+template <int BN>
+__host__ __device__ constexpr size_t tc_smem_bytes() {
+  return 1024 /*alignment slack*/ + (size_t)tc_stages<BN>() * (kBM + BN) * kStageKBytes +
+         (2 * tc_stages<BN>() + 2) * 8 + (size_t)BN * 8;
+}
+
+template <int BN, bool TF32>
+__global__ void __launch_bounds__(128, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+               int M, int N, int num_k_tiles, double* __restrict__ C, LegMap Cm, LegMap Cn,
+               int* err) {
+  constexpr int STAGES = tc_stages<BN>();
+  constexpr uint32_t A_BYTES = kBM * kStageKBytes, B_BYTES = BN * kStageKBytes;
+  constexpr int KE = TF32 ? 32 : 64;  // elements of K per stage
+  constexpr uint32_t IDESC = make_idesc(kBM, BN, TF32 ? 2u : 1u);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* done = empty + STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  long long* offCn = reinterpret_cast<long long*>(done + 2);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int n0 = blockIdx.x * BN;
+  const int m0 = blockIdx.y * kBM;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {  // TMEM: BN FP32 columns x 128 lanes
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"((uint32_t)BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  for (int j = threadIdx.x; j < BN; j += blockDim.x) {
+    const long long n = (long long)n0 + j;
+    offCn[j] = n < N ? tc_map_offset(Cn, n) : 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer: TMA
+    for (int kt = 0; kt < num_k_tiles; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t it = kt / STAGES;
+      if (!mbar_wait(&empty[s], (it & 1u) ^ 1u, err)) break;
+      mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+      tma_load_2d(sA + s * A_BYTES, &mapA, &full[s], kt * KE, m0);
+      tma_load_2d(sB + s * B_BYTES, &mapB, &full[s], kt * KE, n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    for (int kt = 0; kt < num_k_tiles; ++kt) {
+      const int s = kt % STAGES;
+      const uint32_t it = kt / STAGES;
+      if (!mbar_wait(&full[s], it & 1u, err)) break;
+      tc_fence_after();
+      const uint64_t adesc = smem_desc_sw128(sA + s * A_BYTES);
+      const uint64_t bdesc = smem_desc_sw128(sB + s * B_BYTES);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)  // 32 bytes of K per instruction
+        umma<TF32>(tmem, adesc + 2ull * k, bdesc + 2ull * k, IDESC, (kt | k) != 0);
+      umma_commit(&empty[s]);
+    }
+    umma_commit(done);
+  }
+  __syncwarp();
+  const bool ok = mbar_wait(done, 0, err);
+  tc_fence_after();
+
+  // epilogue: warp w owns TMEM lanes 32w .. 32w+31 = tile rows
+  const int row = warp * 32 + lane;
+  const long long m = (long long)m0 + row;
+  const long long offm = (m < M) ? tc_map_offset(Cm, m) : 0;
+  if (ok) {
+#pragma unroll 1
+    for (int j0 = 0; j0 < BN; j0 += 32) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)j0, r);
+      if (m < M) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          if (n0 + j0 + i < N) C[offm + offCn[j0 + i]] = (double)__uint_as_float(r[i]);
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)BN));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Packing: out[r * Kp + k] = cast(in[Rm(r) + Rk(k)]), zero for K <= k < Kp
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t y;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(y) : "f"(x));
+  return __uint_as_float(y);
+}
+
+template <bool TF32>
+__global__ void pack_kernel(void* __restrict__ out, const double* __restrict__ in, LegMap Rm,
+                            LegMap Rk, long long R, long long K, long long Kp) {
+  const long long total = R * Kp;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / Kp, k = i - r * Kp;
+    const double v = (k < K) ? in[tc_map_offset(Rm, r) + tc_map_offset(Rk, k)] : 0.0;
+    if constexpr (TF32)
+      static_cast<float*>(out)[i] = round_tf32((float)v);
+    else
+      static_cast<__nv_bfloat16*>(out)[i] = __double2bfloat16(v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
 struct TcGemm {
-  int unused;
+  PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  int* err = nullptr;
 };
 
-TcGemm* tc_create() { return nullptr; }
-void tc_destroy(TcGemm* t) { delete t; }
+TcGemm* tc_create() {
+  TcGemm* t = new (std::nothrow) TcGemm;
+  if (!t) return nullptr;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !fn) {
+    cudaGetLastError();
+    delete t;
+    return nullptr;
+  }
+  t->encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  if (cudaMalloc(&t->err, sizeof(int)) != cudaSuccess || cudaMemset(t->err, 0, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    delete t;
+    return nullptr;
+  }
+  return t;
+}
 
-int tc_contract(TcGemm*, cudaStream_t, int, long long, long long, long long, const double*,
-                const LegMap&, const LegMap&, const double*, const LegMap&, const LegMap&, double*,
-                const LegMap&, const LegMap&, long long*) {
-  return -6;
+void tc_destroy(TcGemm* t) {
+  if (!t) return;
+  if (t->err) cudaFree(t->err);
+  delete t;
+}
+
+int tc_error(TcGemm* t, cudaStream_t s) {
+  int h = 0;
+  if (cudaMemcpyAsync(&h, t->err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return -3;
+  return h;
+}
+
+namespace {
+
+bool make_map(TcGemm* t, CUtensorMap* map, void* base, bool tf32, long long rows, long long Kp,
+              int box_rows) {
+  const cuuint64_t gdim[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  const cuuint64_t gstride[1] = {(cuuint64_t)Kp * (tf32 ? 4 : 2)};
+  const cuuint32_t box[2] = {(cuuint32_t)(tf32 ? 32 : 64), (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = t->encode(map, tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                               2, base, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN, bool TF32>
+cudaError_t launch(cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
+                   int nk, double* C, const LegMap& Cm, const LegMap& Cn, int* err) {
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(tc_gemm_kernel<BN, TF32>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)tc_smem_bytes<BN>());
+  });
+  if (attr_err != cudaSuccess) return attr_err;
+  dim3 grid((N + BN - 1) / BN, (M + kBM - 1) / kBM);
+  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+  tc_gemm_kernel<BN, TF32><<<grid, 128, tc_smem_bytes<BN>(), s>>>(ma, mb, M, N, nk, C, Cm, Cn, err);
+  return cudaGetLastError();
+}
+
+template <bool TF32>
+cudaError_t pack(cudaStream_t s, void* out, const double* in, const LegMap& Rm, const LegMap& Rk,
+                 long long R, long long K, long long Kp) {
+  long long blocks = (R * Kp + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks < 1) blocks = 1;
+  pack_kernel<TF32><<<(unsigned)blocks, 256, 0, s>>>(out, in, Rm, Rk, R, K, Kp);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int tc_contract(TcGemm* t, cudaStream_t s, int precision, long long M, long long N, long long K,
+                const double* A, const LegMap& Am, const LegMap& Ak, const double* B,
+                const LegMap& Bk, const LegMap& Bn, double* C, const LegMap& Cm,
+                const LegMap& Cn, long long* launches, int* err_word) {
+  if (!t) return -6;
+  int* err = err_word ? err_word : t->err;
+  if (M <= 0 || N <= 0) return 0;
+  if (M > (1ll << 31) - 1 || N > (1ll << 31) - 1 || K > (1ll << 30)) return -1;
+  const bool tf32 = precision == 1;
+  const int esz = tf32 ? 4 : 2;
+  const long long Kp = ((K + 7) / 8) * 8;  // 16-byte row pitch
+  void* pa = nullptr;
+  void* pb = nullptr;
+  if (cudaMallocAsync(&pa, (size_t)(M * Kp * esz), s) != cudaSuccess ||
+      cudaMallocAsync(&pb, (size_t)(N * Kp * esz), s) != cudaSuccess) {
+    cudaGetLastError();
+    if (pa) cudaFreeAsync(pa, s);
+    return -2;
+  }
+  cudaError_t e = tf32 ? pack<true>(s, pa, A, Am, Ak, M, K, Kp) : pack<false>(s, pa, A, Am, Ak, M, K, Kp);
+  if (e == cudaSuccess)
+    e = tf32 ? pack<true>(s, pb, B, Bn, Bk, N, K, Kp) : pack<false>(s, pb, B, Bn, Bk, N, K, Kp);
+  *launches += 2;
+  const int BN = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
+  CUtensorMap ma, mb;
+  int rc = 0;
+  if (e != cudaSuccess) {
+    rc = -3;
+  } else if (!make_map(t, &ma, pa, tf32, M, Kp, kBM) || !make_map(t, &mb, pb, tf32, N, Kp, BN)) {
+    rc = -3;
+  } else {
+    const int nk = (int)((Kp + (tf32 ? 32 : 64) - 1) / (tf32 ? 32 : 64));
+    if (tf32) {
+      e = BN == 64    ? launch<64, true>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err)
+          : BN == 128 ? launch<128, true>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err)
+                      : launch<256, true>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err);
+    } else {
+      e = BN == 64    ? launch<64, false>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err)
+          : BN == 128 ? launch<128, false>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err)
+                      : launch<256, false>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err);
+    }
+    ++*launches;
+    if (e != cudaSuccess) rc = -3;
+  }
+  cudaFreeAsync(pa, s);
+  cudaFreeAsync(pb, s);
+  return rc;
 }
 
 }  // namespace ctm

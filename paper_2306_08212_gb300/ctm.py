@@ -42,6 +42,8 @@ SIGNATURES = {
     "ctm_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "ctm_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _D, _D]),
     "ctm_singular_values_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
+    "ctm_contract_test": (ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
+                                          ctypes.c_longlong, _D, _D, _D]),
     "ctm_last_error": (ctypes.c_char_p, [_P]),
     "ctm_free": (None, [_P]),
 }
@@ -209,6 +211,17 @@ def ctm_singular_values_noalloc(M_ptr, rows, cols, s_ptr, stream=None):
     st = stream if stream is not None else _current_stream()
     return load().ctm_singular_values_noalloc(ctypes.c_void_p(M_ptr), int(rows), int(cols),
                                               ctypes.c_void_p(s_ptr), st)
+
+
+def ctm_contract_test(precision, A, B):
+    """C = A @ B through the library's FP64 or tensor-core contraction kernel."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    M, K = A.shape
+    N = B.shape[1]
+    C = np.zeros((M, N))
+    rc = load().ctm_contract_test(int(precision), M, N, K, _dptr(A), _dptr(B), _dptr(C))
+    return rc, C
 
 
 def ctm_last_error(ctx):
