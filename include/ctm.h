@@ -53,6 +53,9 @@ enum { CTM_STANDARD = 0, CTM_REDUCED_SEQUENTIAL = 1 };
 /* Arithmetic of the absorption / renormalisation contractions.  Projector
  * factorisations, normalisation, spectra and observables are FP64 always. */
 enum { CTM_FP64 = 0, CTM_TF32 = 1, CTM_BF16 = 2 };
+/* OR-ed into `precision` of ctm_init_env: fold only (bond dimension D^2), no
+ * growth; for callers that install their own environment with ctm_set_tensor. */
+enum { CTM_INIT_NO_GROW = 0x100 };
 
 /*
  * Create a context, copy A and B (host or device pointers, detected with

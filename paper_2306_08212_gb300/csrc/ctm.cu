@@ -32,7 +32,8 @@ void ck(cudaError_t e, const char* what) {
   if (e != cudaSuccess) fail(CTM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-constexpr int kExactSvdMax = 512;  // exact one-sided Jacobi below this size
+constexpr int kExactSvdMax = 1024;  // exact one-sided Jacobi up to this size
+constexpr int kFastMinSide = 128;   // mixed precision: subspace iteration above this size
 constexpr int kOversample = 16;    // randomized range finder: extra columns
 constexpr int kPowerIters = 2;     // randomized range finder: subspace iterations
 constexpr int kMaxSweeps = 60;
@@ -63,6 +64,12 @@ struct ctm_ctx {
   };
   bool prof_on = false;
   ProfClass prof[4];
+  struct CacheEntry {  // warm start of the mixed-precision subspace iteration
+    double* p = nullptr;
+    int rows = 0, k = 0;
+  };
+  CacheEntry cache[64];
+  int* floored = nullptr;  // CholeskyQR pivots floored (device counter)
 };
 
 namespace {
@@ -308,6 +315,32 @@ Plan make_plan(const Spec& s, const Ten& A, const Ten& B) {
   return p;
 }
 
+// CTM_CHECK=1: after each contraction / factorisation, synchronise and report
+// the first step that produced a non-finite value (debugging aid).
+bool check_on() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = std::getenv("CTM_CHECK");
+    on = (e && *e && *e != '0') ? 1 : 0;
+  }
+  return on == 1;
+}
+
+void check_finite(ctm_ctx* c, const Ten& t, const char* what) {
+  if (!check_on()) return;
+  int* d = c->floored + 1;
+  ck(cudaMemsetAsync(d, 0, sizeof(int), c->stream), "memset");
+  ck(count_nonfinite(c->stream, t.p, t.size(), d), "count");
+  int h = 0;
+  ck(cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, c->stream), "d2h");
+  ck(cudaStreamSynchronize(c->stream), "sync");
+  if (h) {
+    std::fprintf(stderr, "[ctm] non-finite after %s (%d entries, dims", what, h);
+    for (int i = 0; i < t.nd; ++i) std::fprintf(stderr, " %d", t.dims[i]);
+    std::fprintf(stderr, ")\n");
+  }
+}
+
 // C = A . B per the spec, FP64 always (factorisation-side and observables).
 Tmp ein64(ctm_ctx* c, const char* spec, const Ten& A, const Ten& B) {
   Plan p = make_plan(parse(spec), A, B);
@@ -331,6 +364,7 @@ Tmp ein(ctm_ctx* c, const char* spec, const Ten& A, const Ten& B) {
   int rc = tc_contract(c->tc, c->stream, c->precision, p.M, p.N, p.K, A.p, p.Am, p.Ak, B.p,
                        p.Bk, p.Bn, C.t.p, p.Cm, p.Cn, &c->launches, &c->flags->error);
   if (rc != 0) fail(CTM_ERR_CUDA, std::string("tensor-core contraction failed: ") + spec);
+  check_finite(c, C.t, spec);
   return C;
 }
 
@@ -368,6 +402,7 @@ Tmp sorted_unit_columns(ctm_ctx* c, double* X, int nrows, int ncols, int k) {
 // most kExactSvdMax, else a randomized subspace iteration (Halko, Martinsson &
 // Tropp, SIAM Rev. 53, 217 (2011)) with a Jacobi SVD of the projected problem.
 Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k);
+
 
 // CTM_TRACE=1 prints every factorisation (shape, path, time, Jacobi sweeps of
 // the last launch) to stderr; it synchronises the stream around each call.
@@ -506,6 +541,154 @@ Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k) {
 }
 
 // ---------------------------------------------------------------------------
+// Mixed-precision factorisation path
+// ---------------------------------------------------------------------------
+LegMap lm1(int d0, long long s0) {
+  LegMap m;
+  push(m, d0, s0);
+  return m;
+}
+
+void gemm64(ctm_ctx* c, long long M, long long N, long long K, double alpha, const double* A,
+            const LegMap& Am, const LegMap& Ak, const double* B, const LegMap& Bk,
+            const LegMap& Bn, double beta, double* C, const LegMap& Cm, const LegMap& Cn) {
+  ProfScope ps(c, 0, 2.0 * M * N * K);
+  ck(gemm_f64(c->stream, M, N, K, alpha, A, Am, Ak, B, Bk, Bn, beta, C, Cm, Cn), "gemm");
+  ++c->launches;
+}
+
+// Sketch products of the subspace iteration in the context's precision.
+void gemm_mixed(ctm_ctx* c, long long M, long long N, long long K, const double* A,
+                const LegMap& Am, const LegMap& Ak, const double* B, const LegMap& Bk,
+                const LegMap& Bn, double* C, const LegMap& Cm, const LegMap& Cn) {
+  if (c->precision == CTM_FP64) {
+    gemm64(c, M, N, K, 1.0, A, Am, Ak, B, Bk, Bn, 0.0, C, Cm, Cn);
+    return;
+  }
+  ProfScope ps(c, c->precision == CTM_TF32 ? 1 : 2, 2.0 * M * N * K);
+  if (tc_contract(c->tc, c->stream, c->precision, M, N, K, A, Am, Ak, B, Bk, Bn, C, Cm, Cn,
+                  &c->launches, &c->flags->error) != 0)
+    fail(CTM_ERR_CUDA, "tensor-core sketch product failed");
+}
+
+// Orthonormal basis Q (row-major rows x n) of the columns of Y, whose entry
+// (i, j) sits at Y[i * ys_r + j * ys_c], by `passes` CholeskyQR passes in FP64:
+// G = Q^T Q, column scaling D, G' = D^-1 G D^-1 (+ shift on the first pass),
+// blocked Cholesky G' = L L^T (32-wide panels, updates as GEMMs), Q <- Q D^-1 L^-T.
+Tmp cholqr(ctm_ctx* c, const double* Y, long long ys_r, long long ys_c, int rows, int n,
+           int passes) {
+  constexpr int NB = 32;
+  const int nblk = (n + NB - 1) / NB;
+  Tmp Q(c, {rows, n});
+  {
+    LegMap m;
+    push(m, rows, ys_r);
+    push(m, n, ys_c);
+    ck(permute_f64(c->stream, Q.t.p, Y, m), "copy");
+    ++c->launches;
+  }
+  Tmp Qn(c, {rows, n}), G(c, {n, n}), d(c, {n}), Linv(c, {nblk * NB * NB}), P(c, {n, NB}),
+      T(c, {rows, NB});
+  int* defmask = (int*)dalloc(c, (n + 1) / 2 + 1);
+  ck(cudaMemsetAsync(defmask, 0, sizeof(int) * n, c->stream), "mask");
+  const double u = 1.1102230246251565e-16;
+  for (int pass = 0; pass < passes; ++pass) {
+    // G = Q^T Q
+    gemm64(c, n, n, rows, 1.0, Q.t.p, lm1(n, 1), lm1(rows, n), Q.t.p, lm1(rows, n), lm1(n, 1), 0.0,
+           G.t.p, lm1(n, n), lm1(n, 1));
+    const double shift = pass == 0 ? 11.0 * ((double)rows * n + (double)n * (n + 1)) * u : 0.0;
+    ck(gram_scale(c->stream, G.t.p, n, d.t.p, shift), "gram scale");
+    ++c->launches;
+    for (int j0 = 0; j0 < n; j0 += NB) {
+      const int jb = std::min(NB, n - j0);
+      double* Lj = Linv.t.p + (long long)(j0 / NB) * NB * NB;
+      // unshifted passes: a pivot below 1e-12 (of the unit scaled diagonal) marks a
+      // column that lies in the span of the earlier ones; it is replaced below
+      ck(chol_diag(c->stream, G.t.p, n, j0, jb, Lj, 1e-28, c->floored, pass == 0 ? 0.0 : 1e-12,
+                   pass == 0 ? nullptr : defmask),
+         "chol diag");
+      ++c->launches;
+      const int m2 = n - j0 - jb;
+      if (m2 > 0) {
+        double* A21 = G.t.p + (long long)(j0 + jb) * n + j0;
+        gemm64(c, m2, jb, jb, 1.0, A21, lm1(m2, n), lm1(jb, 1), Lj, lm1(jb, 1), lm1(jb, NB), 0.0,
+               P.t.p, lm1(m2, NB), lm1(jb, 1));
+        ck(copy2d(c->stream, A21, n, P.t.p, NB, m2, jb, nullptr, 0), "copy");
+        ++c->launches;
+        double* G22 = G.t.p + (long long)(j0 + jb) * n + j0 + jb;
+        gemm64(c, m2, m2, jb, -1.0, P.t.p, lm1(m2, NB), lm1(jb, 1), P.t.p, lm1(jb, 1),
+               lm1(m2, NB), 1.0, G22, lm1(m2, n), lm1(m2, 1));
+      }
+    }
+    for (int j0 = 0; j0 < n; j0 += NB) {
+      const int jb = std::min(NB, n - j0);
+      ck(copy2d(c->stream, T.t.p, NB, Q.t.p + j0, n, rows, jb, d.t.p, j0), "copy");
+      ++c->launches;
+      if (j0 > 0)
+        gemm64(c, rows, jb, j0, -1.0, Qn.t.p, lm1(rows, n), lm1(j0, 1), G.t.p + (long long)j0 * n,
+               lm1(j0, 1), lm1(jb, n), 1.0, T.t.p, lm1(rows, NB), lm1(jb, 1));
+      const double* Lj = Linv.t.p + (long long)(j0 / NB) * NB * NB;
+      gemm64(c, rows, jb, jb, 1.0, T.t.p, lm1(rows, NB), lm1(jb, 1), Lj, lm1(jb, 1), lm1(jb, NB),
+             0.0, Qn.t.p + j0, lm1(rows, n), lm1(jb, 1));
+    }
+    std::swap(Q, Qn);
+    if (pass > 0 && pass + 1 < passes) {  // rank deficiency: random columns, orthonormalised next
+      ck(replace_flagged(c->stream, Q.t.p, rows, n, defmask, c->seed++), "replace");
+      ++c->launches;
+    }
+    check_finite(c, Q.t, pass == 0 ? "cholqr pass 1" : "cholqr pass >1");
+  }
+  dfree(c, defmask);
+  return Q;
+}
+
+constexpr int kColdIters = 2;  // power iterations without a cached subspace
+constexpr int kWarmIters = 1;  // with the subspace cached at this position
+
+// Leading-k left singular subspace of M (row-major rows x cols) by subspace
+// iteration: Q <- orth(M (M^T Q)), products on the tensor cores in the
+// context's precision, orthonormalisation by FP64 CholeskyQR.  The basis of the
+// previous call at the same position (`slot`) is the starting block when it
+// fits, otherwise a Gaussian sketch.  Only the subspace matters for a
+// projector v v^T, so the basis is returned as it comes.
+Tmp left_svd_power(ctm_ctx* c, const double* M, int rows, int cols, int k, int slot) {
+  auto& ce = c->cache[slot];
+  Tmp Q;
+  int iters = kWarmIters;
+  if (ce.p && ce.rows == rows && ce.k == k) {
+    Q = Tmp(c, {rows, k});
+    ck(cudaMemcpyAsync(Q.t.p, ce.p, sizeof(double) * rows * k, cudaMemcpyDeviceToDevice, c->stream),
+       "cache");
+  } else {
+    iters = kColdIters;
+    Tmp Om(c, {cols, k});
+    ck(gaussian_fill(c->stream, Om.t.p, (long long)cols * k, c->seed++), "gaussian");
+    ++c->launches;
+    Tmp Y(c, {rows, k});
+    gemm_mixed(c, rows, k, cols, M, lm1(rows, cols), lm1(cols, 1), Om.t.p, lm1(cols, k),
+               lm1(k, 1), Y.t.p, lm1(rows, k), lm1(k, 1));
+    Q = cholqr(c, Y.t.p, k, 1, rows, k, 4);
+  }
+  for (int it = 0; it < iters; ++it) {
+    Tmp Z(c, {cols, k});
+    gemm_mixed(c, cols, k, rows, M, lm1(cols, 1), lm1(rows, cols), Q.t.p, lm1(rows, k), lm1(k, 1),
+               Z.t.p, lm1(cols, k), lm1(k, 1));
+    Tmp Y(c, {rows, k});
+    gemm_mixed(c, rows, k, cols, M, lm1(rows, cols), lm1(cols, 1), Z.t.p, lm1(cols, k), lm1(k, 1),
+               Y.t.p, lm1(rows, k), lm1(k, 1));
+    Q = cholqr(c, Y.t.p, k, 1, rows, k, 4);
+  }
+  if (!ce.p || ce.rows != rows || ce.k != k) {
+    ce.p = owned_alloc(c, (long long)rows * k);
+    ce.rows = rows;
+    ce.k = k;
+  }
+  ck(cudaMemcpyAsync(ce.p, Q.t.p, sizeof(double) * rows * k, cudaMemcpyDeviceToDevice, c->stream),
+     "cache");
+  return Q;
+}
+
+// ---------------------------------------------------------------------------
 // Environment access
 // ---------------------------------------------------------------------------
 inline int slot_of(int k, int r) { return (k - 1 + r) % 4; }  // stored k-1 index
@@ -595,7 +778,11 @@ Proj projector_standard(ctm_ctx* c, int r, int x) {
   const int rows = na * D * D, cols = D * D * nb;
   const int k = std::min(c->chi, rows);
   Proj P;
-  Tmp U = left_svd(c, Q.t.p, rows, cols, k);
+  const bool fast = c->precision != CTM_FP64 && std::min(rows, cols) > kFastMinSide && k < rows &&
+                    k <= cols;
+  // mixed precision: subspace iteration (cache slots 48.. for the standard projectors)
+  Tmp U = fast ? left_svd_power(c, Q.t.p, rows, cols, k, 48 + r * 2 + x)
+               : left_svd(c, Q.t.p, rows, cols, k);
   P.v = std::move(U);
   P.v.t = view(P.v.t, {na, D, D, k});
   return P;
@@ -603,14 +790,21 @@ Proj projector_standard(ctm_ctx* c, int r, int x) {
 
 // Split isometries from a 4-leg network Mt[alpha, k, b, beta] (Sec. IV, Fig. 4a).
 // Also returns N = v1^T Mt (for reuse by the caller).
-void split_projector(ctm_ctx* c, const Ten& Mt, Tmp& v1, Tmp& v2, Tmp& N) {
+void split_projector(ctm_ctx* c, const Ten& Mt, Tmp& v1, Tmp& v2, Tmp& N, int slot) {
   const int na = Mt.dims[0], D = Mt.dims[1], nb = Mt.dims[3];
   const int k1 = std::min(c->chip, na * D);
-  v1 = left_svd(c, Mt.p, na * D, D * nb, k1);
+  const bool fast = c->precision != CTM_FP64 && std::min(na * D, D * nb) > kFastMinSide;
+  if (fast && k1 < na * D && k1 <= D * nb)
+    v1 = left_svd_power(c, Mt.p, na * D, D * nb, k1, slot);
+  else
+    v1 = left_svd(c, Mt.p, na * D, D * nb, k1);
   v1.t = view(v1.t, {na, D, k1});
   N = ein64(c, "akc,akbz->cbz", v1, Mt);
   const int k2 = std::min(c->chi, k1 * D);
-  v2 = left_svd(c, N.t.p, k1 * D, nb, k2);
+  if (fast && k2 == nb && k2 < k1 * D)  // keeps the whole column space: any orthonormal basis
+    v2 = cholqr(c, N.t.p, nb, 1, k1 * D, nb, 4);
+  else
+    v2 = left_svd(c, N.t.p, k1 * D, nb, k2);
   v2.t = view(v2.t, {k1, D, k2});
 }
 
@@ -645,7 +839,8 @@ Tmp absorb_edge_seq(ctm_ctx* c, const Ten& T, const Ten& S, const char* roles, c
 }
 
 // Reduced-network projector of the bond below x (Sec. III-IV, Fig. 3c, Fig. 8).
-Proj projector_seq(ctm_ctx* c, int r, int x) {
+Proj projector_seq(ctm_ctx* c, int r, int x, int col) {
+  const int base = ((r * 2 + col) * 2 + x) * 3;
   Ten S;
   site(c, r, x, S);
   Ten C1 = E(c, 0, 1, x, r), T1 = E(c, 1, 1, x, r);
@@ -654,11 +849,11 @@ Proj projector_seq(ctm_ctx* c, int r, int x) {
   Tmp vl1, vl2, Nl, vr1, vr2, Nr;
   {
     Tmp L = ein64(c, "dg,akbd->gkba", C1, T1);
-    split_projector(c, L, vl1, vl2, Nl);
+    split_projector(c, L, vl1, vl2, Nl, base + 0);
   }
   {
     Tmp R = ein64(c, "ez,zkbw->ekbw", C2, T3);
-    split_projector(c, R, vr1, vr2, Nr);
+    split_projector(c, R, vr1, vr2, Nr, base + 1);
   }
   Tmp C1p = ein64(c, "cby,cba->ya", vl2, Nl);
   Tmp C2p = ein64(c, "cby,cbw->yw", vr2, Nr);
@@ -672,15 +867,15 @@ Proj projector_seq(ctm_ctx* c, int r, int x) {
   Xm.release();
   Proj P;
   Tmp N;
-  split_projector(c, M, P.v1, P.v2, N);
+  split_projector(c, M, P.v1, P.v2, N, base + 2);
   return P;
 }
 
 // One column absorption in frame r (Sec. II, Fig. 2a-b).
-void column_absorb(ctm_ctx* c, int r, int mode) {
+void column_absorb(ctm_ctx* c, int r, int mode, int col) {
   Proj P[2];
   for (int x = 0; x < 2; ++x)
-    P[x] = (mode == CTM_STANDARD) ? projector_standard(c, r, x) : projector_seq(c, r, x);
+    P[x] = (mode == CTM_STANDARD) ? projector_standard(c, r, x) : projector_seq(c, r, x, col);
   Tmp newT[2], newC1[2], newC4[2];
   for (int x = 0; x < 2; ++x) {
     const int y = other(x);
@@ -735,8 +930,8 @@ void check_flags(ctm_ctx* c) {
 }
 
 void do_move(ctm_ctx* c, int dir, int mode) {
-  column_absorb(c, dir, mode);
-  column_absorb(c, dir, mode);
+  column_absorb(c, dir, mode, 0);
+  column_absorb(c, dir, mode, 1);
   check_flags(c);
 }
 
@@ -967,6 +1162,8 @@ extern "C" {
 int ctm_init_env(ctm_ctx** out, const double* A, const double* B, int d, int D, int chi,
                  int chi_prime, int precision, const double* boundary, void* stream) {
   if (!out || !A || !B || d < 1 || D < 1 || chi < 1 || chi_prime < 0) return CTM_ERR_ARG;
+  const bool no_grow = (precision & CTM_INIT_NO_GROW) != 0;
+  precision &= ~CTM_INIT_NO_GROW;
   if (precision != CTM_FP64 && precision != CTM_TF32 && precision != CTM_BF16) return CTM_ERR_ARG;
   if ((long long)chi * D * D * chi > (1ll << 31)) return CTM_ERR_ARG;
   *out = nullptr;
@@ -993,6 +1190,8 @@ int ctm_init_env(ctm_ctx** out, const double* A, const double* B, int d, int D, 
     c->flags = (DevFlags*)f;
     ck(cudaMemsetAsync(c->flags, 0, sizeof(DevFlags), c->stream), "flags");
     c->norm_scratch = owned_alloc(c, kNormScratch);
+    c->floored = (int*)owned_alloc(c, 1);  // two ints: floored pivots, scratch counter
+    ck(cudaMemsetAsync(c->floored, 0, 2 * sizeof(int), c->stream), "floored");
     if (precision != CTM_FP64) {
       c->tc = tc_create();
       if (!c->tc) fail(CTM_ERR_UNSUPPORTED, "tensor-core GEMM unavailable");
@@ -1031,7 +1230,7 @@ int ctm_init_env(ctm_ctx** out, const double* A, const double* B, int d, int D, 
                 owned_alloc(c, kind == 0 ? (long long)cmax * cmax : (long long)cmax * D * D * cmax);
     fold_init(c);
     check_flags(c);
-    grow(c);
+    if (!no_grow) grow(c);
   });
   if (rc != CTM_OK) {
     ctm_free(c);

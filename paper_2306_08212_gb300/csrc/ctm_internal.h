@@ -57,12 +57,13 @@ struct DevFlags {
   unsigned int bar_count;
   unsigned int bar_gen;
   unsigned long long off_max[2];  // per-sweep max off-diagonal cosine (bits of a double >= 0)
+  double fro2;                    // squared Frobenius norm of the Jacobi input
   int error;                      // sticky: a grid barrier timed out
   int noconv;                     // sticky: a Jacobi sweep cap was reached
   int bad;                        // sticky: a normalised tensor was zero or not finite
   int sweeps;                     // sweeps used by the last Jacobi launch
 };
-constexpr size_t kDevFlagsResetBytes = 24;  // offsetof(DevFlags, error)
+constexpr size_t kDevFlagsResetBytes = 32;  // offsetof(DevFlags, error)
 
 // ---- kernels (gemm_f64.cu) ----
 // C(m,n) = alpha * sum_k A(m,k) B(k,n) + beta * C(m,n), all FP64, every operand
@@ -107,5 +108,17 @@ constexpr int kNormScratch = 305;
 cudaError_t normalize_f64(cudaStream_t s, double* x, long long n, double* scratch, int* bad);
 
 cudaError_t fill_identity(cudaStream_t s, double* x, int n);
+
+// Adds the number of non-finite entries of x[0..n) to *out (device).
+cudaError_t count_nonfinite(cudaStream_t s, const double* x, long long n, int* out);
+
+// Blocked-Cholesky pieces (CholeskyQR).
+cudaError_t chol_diag(cudaStream_t s, double* G, int lda, int j0, int jb, double* Linv,
+                      double floor, int* floored, double tau, int* defmask);
+cudaError_t replace_flagged(cudaStream_t s, double* Q, int rows, int n, int* defmask,
+                            unsigned long long seed);
+cudaError_t gram_scale(cudaStream_t s, double* G, int n, double* d, double shift_rel);
+cudaError_t copy2d(cudaStream_t s, double* dst, long long dld, const double* src, long long sld,
+                   int rows, int cols, const double* colscale, int c0);
 
 }  // namespace ctm

@@ -23,7 +23,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 gemm_f64_kernel(long long M, long long N, long long K, double alpha, const double* __restrict__ A,
                 LegMap Am, LegMap Ak, const double* __restrict__ B, LegMap Bk, LegMap Bn,
                 double beta, double* __restrict__ C, LegMap Cm, LegMap Cn, int a_m_fast,
-                int b_n_fast) {
+                int b_n_fast, long long kchunk, double* __restrict__ partial) {
   constexpr int NT = (BM / TM) * (BN / TN);
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
@@ -52,24 +52,26 @@ gemm_f64_kernel(long long M, long long N, long long K, double alpha, const doubl
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = 0.0;
 
-  for (long long k0 = 0; k0 < K; k0 += BK) {
+  const long long kbeg = (long long)blockIdx.z * kchunk;
+  const long long kend = kbeg + kchunk < K ? kbeg + kchunk : K;
+  for (long long k0 = kbeg; k0 < kend; k0 += BK) {
     __syncthreads();
     for (int i = tid; i < BK; i += NT) {
       const long long k = k0 + i;
-      offAk[i] = k < K ? map_offset(Ak, k) : 0;
-      offBk[i] = k < K ? map_offset(Bk, k) : 0;
+      offAk[i] = k < kend ? map_offset(Ak, k) : 0;
+      offBk[i] = k < kend ? map_offset(Bk, k) : 0;
     }
     __syncthreads();
     for (int t = tid; t < BM * BK; t += NT) {
       const int mm = a_m_fast ? t % BM : t / BK;
       const int kk = a_m_fast ? t / BM : t % BK;
-      const bool ok = (m0 + mm < M) && (k0 + kk < K);
+      const bool ok = (m0 + mm < M) && (k0 + kk < kend);
       As[kk][mm] = ok ? A[offAm[mm] + offAk[kk]] : 0.0;
     }
     for (int t = tid; t < BN * BK; t += NT) {
       const int nn = b_n_fast ? t % BN : t / BK;
       const int kk = b_n_fast ? t / BN : t % BK;
-      const bool ok = (n0 + nn < N) && (k0 + kk < K);
+      const bool ok = (n0 + nn < N) && (k0 + kk < kend);
       Bs[kk][nn] = ok ? B[offBk[kk] + offBn[nn]] : 0.0;
     }
     __syncthreads();
@@ -94,14 +96,32 @@ gemm_f64_kernel(long long M, long long N, long long K, double alpha, const doubl
     for (int j = 0; j < TN; ++j) {
       const int nn = tx * TN + j;
       if (n0 + nn >= N) continue;
-      double* c = C + offCm[mm] + offCn[nn];
       const double v = alpha * acc[i][j];
+      if (partial) {  // split-K: dense partial tile, reduced in a fixed order later
+        partial[((long long)blockIdx.z * M + m0 + mm) * N + n0 + nn] = v;
+        continue;
+      }
+      double* c = C + offCm[mm] + offCn[nn];
       *c = (beta == 0.0) ? v : fma(beta, *c, v);
     }
   }
 }
 
 static int innermost_unit(const LegMap& m) { return m.n > 0 && m.stride[m.n - 1] == 1; }
+
+__global__ void splitk_reduce_kernel(const double* __restrict__ partial, int splits, long long M,
+                                     long long N, double beta, double* __restrict__ C, LegMap Cm,
+                                     LegMap Cn) {
+  const long long MN = M * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < MN;
+       i += (long long)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int z = 0; z < splits; ++z) v += partial[z * MN + i];
+    const long long m = i / N, n = i - m * N;
+    double* c = C + map_offset(Cm, m) + map_offset(Cn, n);
+    *c = (beta == 0.0) ? v : fma(beta, *c, v);
+  }
+}
 
 cudaError_t gemm_f64(cudaStream_t s, long long M, long long N, long long K, double alpha,
                      const double* A, const LegMap& Am, const LegMap& Ak, const double* B,
@@ -115,12 +135,38 @@ cudaError_t gemm_f64(cudaStream_t s, long long M, long long N, long long K, doub
     dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
     if (grid.y > 65535) return cudaErrorInvalidConfiguration;
     gemm_f64_kernel<64, 64, 16, 4, 4><<<grid, 256, 0, s>>>(M, N, K, alpha, A, Am, Ak, B, Bk, Bn,
-                                                           beta, C, Cm, Cn, a_m_fast, b_n_fast);
-  } else {
-    dim3 grid((unsigned)((N + 31) / 32), (unsigned)((M + 31) / 32));
-    if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-    gemm_f64_kernel<32, 32, 16, 2, 2><<<grid, 256, 0, s>>>(M, N, K, alpha, A, Am, Ak, B, Bk, Bn,
-                                                           beta, C, Cm, Cn, a_m_fast, b_n_fast);
+                                                           beta, C, Cm, Cn, a_m_fast, b_n_fast, K,
+                                                           nullptr);
+    return cudaGetLastError();
+  }
+  const long long tiles32 = ((M + 31) / 32) * ((N + 31) / 32);
+  // few output tiles and a long K: split K over more blocks, reduce deterministically
+  long long splits = 1;
+  if (tiles32 < 2 * 152 && K >= 512) {
+    splits = (2 * 152 + tiles32 - 1) / tiles32;
+    const long long kmax = K / 256;
+    if (splits > kmax) splits = kmax;
+    if (splits > 64) splits = 64;
+    if (splits < 1) splits = 1;
+  }
+  const long long kchunk = ((K + splits - 1) / splits + 15) / 16 * 16;
+  splits = (K + kchunk - 1) / kchunk;
+  dim3 grid((unsigned)((N + 31) / 32), (unsigned)((M + 31) / 32), (unsigned)splits);
+  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+  double* partial = nullptr;
+  if (splits > 1) {
+    cudaError_t e = cudaMallocAsync(&partial, sizeof(double) * splits * M * N, s);
+    if (e != cudaSuccess) return e;
+  }
+  gemm_f64_kernel<32, 32, 16, 2, 2><<<grid, 256, 0, s>>>(M, N, K, alpha, A, Am, Ak, B, Bk, Bn,
+                                                         beta, C, Cm, Cn, a_m_fast, b_n_fast,
+                                                         kchunk, partial);
+  if (splits > 1) {
+    long long blocks = (M * N + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    splitk_reduce_kernel<<<(unsigned)blocks, 256, 0, s>>>(partial, (int)splits, M, N, beta, C,
+                                                          Cm, Cn);
+    cudaFreeAsync(partial, s);
   }
   return cudaGetLastError();
 }

@@ -88,6 +88,19 @@ jacobi_kernel(double* __restrict__ X, int nrows, int ncols, int npad, double* __
               DevFlags* fl, int max_sweeps, double tol) {
   const unsigned nblocks = gridDim.x;
   const int npairs = npad / 2;
+  // columns whose squared norm is below 1e-32 ||X||_F^2 lie under FP64
+  // resolution: they are still rotated but do not count for convergence
+  {
+    double part = 0.0, z1 = 0.0, z2 = 0.0;
+    const long long total = (long long)nrows * ncols;
+    for (long long e = blockIdx.x * (long long)kJacobiThreads + threadIdx.x; e < total;
+         e += (long long)gridDim.x * kJacobiThreads)
+      part = fma(X[e], X[e], part);
+    block_sum3<kJacobiThreads>(part, z1, z2);
+    if (threadIdx.x == 0 && part > 0.0) atomicAdd(&fl->fro2, part);
+    if (!grid_barrier(fl, nblocks)) return;
+  }
+  const double tiny = 1e-32 * (*(volatile double*)&fl->fro2);
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     double local_max = 0.0;
     for (int step = 0; step < npad - 1; ++step) {
@@ -110,9 +123,9 @@ jacobi_kernel(double* __restrict__ X, int nrows, int ncols, int npad, double* __
           g = fma(u, v, g);
         }
         block_sum3<kJacobiThreads>(a, b, g);
-        if (a == 0.0 || b == 0.0) continue;
+        if (!(a > 0.0) || !(b > 0.0)) continue;
         const double cosang = fabs(g) / (sqrt(a) * sqrt(b));
-        local_max = fmax(local_max, cosang);
+        if (a > tiny && b > tiny) local_max = fmax(local_max, cosang);
         if (!(cosang > tol)) continue;
         const double zeta = (b - a) / (2.0 * g);
         const double t = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
@@ -328,6 +341,164 @@ cudaError_t normalize_f64(cudaStream_t s, double* x, long long n, double* scratc
   sumsq_partial_kernel<<<kNormBlocks, 256, 0, s>>>(x, n, scratch);
   scale_by_norm_kernel<<<kNormBlocks, 256, 0, s>>>(x, n, scratch, kNormBlocks,
                                                    scratch + kNormBlocks, bad);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Blocked Cholesky pieces (CholeskyQR): a 32x32 diagonal block factorised by
+// one CTA (pivots floored at `floor`, counted in *floored), its triangular
+// inverse, Gram scaling by the column norms with an optional diagonal shift
+// (shifted CholeskyQR: Fukaya, Kannan, Nakatsukasa, Yamamoto & Yanagisawa,
+// SIAM J. Sci. Comput. 42, A477 (2020)), and a strided copy.
+// ---------------------------------------------------------------------------
+__global__ void chol_diag_kernel(double* __restrict__ G, int lda, int j0, int jb,
+                                 double* __restrict__ Linv, double floor, int* floored,
+                                 double tau, int* __restrict__ defmask) {
+  __shared__ double L[32][33];
+  const int t = threadIdx.x;  // 256 threads
+  for (int e = t; e < 32 * 32; e += blockDim.x) {
+    const int i = e / 32, j = e % 32;
+    L[i][j] = (i < jb && j < jb && j <= i) ? G[(long long)(j0 + i) * lda + j0 + j] : 0.0;
+  }
+  __syncthreads();
+  __shared__ int s_def;
+  for (int k = 0; k < jb; ++k) {
+    if (t == 0) {
+      double dkk = L[k][k];
+      s_def = 0;
+      if (defmask && !(dkk > tau)) {
+        // column k is (numerically) in the span of the earlier ones: decouple it
+        // (unit pivot, no elimination) and mark it for replacement
+        defmask[j0 + k] = 1;
+        s_def = 1;
+        dkk = 1.0;
+      } else if (!(dkk > floor)) {
+        dkk = floor;
+        atomicAdd(floored, 1);
+      }
+      L[k][k] = sqrt(dkk);
+    }
+    __syncthreads();
+    const double piv = L[k][k];
+    for (int i = k + 1 + t; i < jb; i += blockDim.x) L[i][k] = s_def ? 0.0 : L[i][k] / piv;
+    __syncthreads();
+    for (int e = t; e < 32 * 32; e += blockDim.x) {
+      const int i = e / 32, j = e % 32;
+      if (j > k && j <= i && i < jb) L[i][j] -= L[i][k] * L[j][k];
+    }
+    __syncthreads();
+  }
+  // write L (lower) back, zero above the diagonal inside the block
+  for (int e = t; e < jb * jb; e += blockDim.x) {
+    const int i = e / jb, j = e % jb;
+    G[(long long)(j0 + i) * lda + j0 + j] = (j <= i) ? L[i][j] : 0.0;
+  }
+  // inverse of the lower-triangular block by forward substitution, one column per thread
+  if (t < jb) {
+    const int cidx = t;
+    double x[32];
+    for (int i = 0; i < jb; ++i) {
+      double acc = (i == cidx) ? 1.0 : 0.0;
+      for (int k = cidx; k < i; ++k) acc -= L[i][k] * x[k];
+      x[i] = (i >= cidx) ? acc / L[i][i] : 0.0;
+    }
+    for (int i = 0; i < 32; ++i) Linv[i * 32 + cidx] = (i < jb) ? x[i] : 0.0;
+  }
+}
+
+cudaError_t chol_diag(cudaStream_t s, double* G, int lda, int j0, int jb, double* Linv,
+                      double floor, int* floored, double tau, int* defmask) {
+  chol_diag_kernel<<<1, 256, 0, s>>>(G, lda, j0, jb, Linv, floor, floored, tau, defmask);
+  return cudaGetLastError();
+}
+
+// Replace every column j of Q (row-major rows x n) with defmask[j] set by
+// Gaussian values, then clear the mask.  One block per column.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z);
+
+__global__ void replace_flagged_kernel(double* __restrict__ Q, int rows, int n,
+                                       int* __restrict__ defmask, unsigned long long seed) {
+  const int j = blockIdx.x;
+  if (!defmask[j]) return;
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+    const unsigned long long base =
+        seed * 0xD1B54A32D192ED03ull + 2ull * ((unsigned long long)j * rows + i);
+    const unsigned long long z1 = splitmix64(base), z2 = splitmix64(base + 1ull);
+    const double u1 = ((double)(z1 >> 11) + 1.0) * 0x1.0p-53;
+    const double u2 = (double)(z2 >> 11) * 0x1.0p-53;
+    Q[(long long)i * n + j] = sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) defmask[j] = 0;
+}
+
+cudaError_t replace_flagged(cudaStream_t s, double* Q, int rows, int n, int* defmask,
+                            unsigned long long seed) {
+  replace_flagged_kernel<<<n, 256, 0, s>>>(Q, rows, n, defmask, seed);
+  return cudaGetLastError();
+}
+
+// d[i] = sqrt(G[i][i]) (or 1 if zero); G[i][j] /= d[i] d[j]; G[i][i] += shift_rel * trace-normalised
+__global__ void gram_scale_kernel(double* __restrict__ G, int n, double* __restrict__ d,
+                                  double shift_rel) {
+  __shared__ double s_tr;
+  if (threadIdx.x == 0) s_tr = 0.0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double g = G[(long long)i * n + i];
+    d[i] = g > 0.0 ? sqrt(g) : 1.0;
+  }
+  __syncthreads();
+  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
+    const long long i = e / n, j = e % n;
+    G[e] /= d[i] * d[j];
+  }
+  __syncthreads();
+  // after scaling every nonzero diagonal is 1, so the trace is n: shift = shift_rel * n
+  for (int i = threadIdx.x; i < n; i += blockDim.x) G[(long long)i * n + i] += shift_rel * n;
+}
+
+cudaError_t gram_scale(cudaStream_t s, double* G, int n, double* d, double shift_rel) {
+  gram_scale_kernel<<<1, 1024, 0, s>>>(G, n, d, shift_rel);
+  return cudaGetLastError();
+}
+
+// dst[r * dld + c] = src[r * sld + c] * (colscale ? 1 / colscale[c0 + c] : 1), r < rows, c < cols
+__global__ void copy2d_kernel(double* __restrict__ dst, long long dld, const double* __restrict__ src,
+                              long long sld, int rows, int cols, const double* __restrict__ colscale,
+                              int c0) {
+  const long long n = (long long)rows * cols;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / cols, c = e % cols;
+    double v = src[r * sld + c];
+    if (colscale) v /= colscale[c0 + c];
+    dst[r * dld + c] = v;
+  }
+}
+
+cudaError_t copy2d(cudaStream_t s, double* dst, long long dld, const double* src, long long sld,
+                   int rows, int cols, const double* colscale, int c0) {
+  long long blocks = ((long long)rows * cols + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  if (blocks < 1) blocks = 1;
+  copy2d_kernel<<<(unsigned)blocks, 256, 0, s>>>(dst, dld, src, sld, rows, cols, colscale, c0);
+  return cudaGetLastError();
+}
+
+__global__ void count_nonfinite_kernel(const double* __restrict__ x, long long n, int* out) {
+  int bad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    bad += !isfinite(x[i]);
+  if (bad) atomicAdd(out, bad);
+}
+
+cudaError_t count_nonfinite(cudaStream_t s, const double* x, long long n, int* out) {
+  long long blocks = (n + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  if (blocks < 1) blocks = 1;
+  count_nonfinite_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, n, out);
   return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@ OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NAN, ERR_NOCONV, ERR_UNSUPPORTED = 0, -1, -2
 LEFT, UP, RIGHT, DOWN = 0, 1, 2, 3
 STANDARD, REDUCED_SEQUENTIAL = 0, 1
 FP64, TF32, BF16 = 0, 1, 2
+INIT_NO_GROW = 0x100
 DIRS = {"left": LEFT, "up": UP, "right": RIGHT, "down": DOWN}
 MODES = {"standard": STANDARD, "reduced_sequential": REDUCED_SEQUENTIAL}
 PRECISIONS = {"fp64": FP64, "tf32": TF32, "bf16": BF16}
