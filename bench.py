@@ -160,6 +160,16 @@ def fp64_gemm_peak():
 
 
 def run_native(args):
+    import torch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    # a side stream: the library can then capture steady-state moves in CUDA graphs
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        return _run_native(args)
+
+
+def _run_native(args):
     import numpy as np
     import torch
 
@@ -179,15 +189,24 @@ def run_native(args):
             rc = ctm.ctm_move(ctx, d, ctm.REDUCED_SEQUENTIAL)
             if rc != ctm.OK:
                 raise RuntimeError(ctm.ctm_last_error(ctx))
-        for corner in range(8):  # convergence check: FP64 corner spectra
-            rc, _ = ctm.ctm_corner_spectrum(ctx, corner, args.chi + 16)
-            if rc != ctm.OK:
-                raise RuntimeError(ctm.ctm_last_error(ctx))
+        # convergence check: FP64 singular values of the 8 corners
+        rc, _ = ctm.ctm_corner_spectra(ctx, args.chi + 16)
+        if rc != ctm.OK:
+            raise RuntimeError(ctm.ctm_last_error(ctx))
 
     for _ in range(args.warmup):
         step()
+    # one untimed step with every class timed: the per-class breakdown, and the
+    # class with the most device time among the contractions
+    ctm.ctm_kernel_stats_reset(ctx, 0xF)
+    step()
+    breakdown = ctm.ctm_kernel_stats(ctx)
+    gemm_like = [k for k in breakdown if k["flops"] > 0]
+    top = max(gemm_like, key=lambda k: k["ms"]) if gemm_like else None
+    top_cls = {v: k for k, v in ctm.PROFILE_CLASSES.items()}[top["name"]] if top else None
     torch.cuda.synchronize()
-    ctm.ctm_kernel_stats_reset(ctx)
+    # timed region: events only around the launches of that class
+    ctm.ctm_kernel_stats_reset(ctx, (1 << top_cls) if top_cls is not None else 0)
     launches0 = ctm.ctm_kernel_launches(ctx)
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
     barrier(dist)
@@ -195,11 +214,13 @@ def run_native(args):
     clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("ctm_timed")  # lets ncu capture exactly the timed steps
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     barrier(dist)
     clk = clocks.stop()
     t = e0.elapsed_time(e1) / 1e3
@@ -259,6 +280,8 @@ def run_native(args):
         "e2e": {"value": moves / t_e2e, "unit": "moves/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
+        "kernel_classes": {k["name"]: {"launches": k["count"], "ms_per_step": k["ms"]}
+                           for k in breakdown},
         "clocks": clk,
         "roofline": roof,
     }

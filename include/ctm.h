@@ -109,6 +109,13 @@ int ctm_expect_bond(ctm_ctx* ctx, int bond, const double* op, double* value);
 int ctm_corner_spectrum(ctm_ctx* ctx, int corner, double* s, int* len);
 
 /*
+ * All 8 corner spectra at once (same order and scaling as ctm_corner_spectrum),
+ * with one batched Jacobi launch when the corners share a shape.  s is a host
+ * buffer of 8 * maxlen doubles (row i = corner i); lens[8] receives the counts.
+ */
+int ctm_corner_spectra(ctm_ctx* ctx, double* s, int maxlen, int* lens);
+
+/*
  * Per-site log norm ln kappa = (1/4) ln[Z22 Z00 / (Z20 Z02)] from the 2x2
  * window with top-left site a, where Zhw closes the environment around an
  * h x w block of sites (corner and edge normalisations cancel).  For the
@@ -136,7 +143,8 @@ long long ctm_kernel_launches(ctm_ctx* ctx);
  * Per-class kernel timing with CUDA events recorded on the context's stream
  * around every launch of a class (0 = FP64 contraction, 1 = TF32 tensor-core
  * contraction, 2 = BF16 tensor-core contraction, 3 = Jacobi SVD sweep kernel).
- * ctm_profile_enable(ctx, 1) clears the counters and starts recording; 0 stops.
+ * ctm_profile_enable(ctx, mask) clears the counters and records the classes
+ * whose bit (1 << class) is set in mask; 0 stops.
  * ctm_profile_read synchronises the stream and returns, for one class, the
  * launches, their summed device time in ms and their algorithmic flop count
  * (2 M N K for a contraction, 0 for Jacobi whose work depends on the data).

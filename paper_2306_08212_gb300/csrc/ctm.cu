@@ -62,7 +62,7 @@ struct ctm_ctx {
     long long count = 0;
     double ms = 0.0, flops = 0.0;
   };
-  bool prof_on = false;
+  int prof_mask = 0;  // bit cls set: time that class
   ProfClass prof[4];
   struct CacheEntry {  // warm start of the mixed-precision subspace iteration
     double* p = nullptr;
@@ -70,6 +70,19 @@ struct ctm_ctx {
   };
   CacheEntry cache[64];
   int* floored = nullptr;  // CholeskyQR pivots floored (device counter)
+  // CUDA graphs of steady-state moves (mixed precision, reduced-sequential)
+  struct GraphEvent {
+    int cls;
+    cudaEvent_t e0, e1;
+    double flops;
+  };
+  bool graphs_ok = true;
+  bool capturing = false;
+  int capture_dir = -1;
+  bool warm[4] = {false, false, false, false};
+  cudaGraphExec_t gexec[4] = {nullptr, nullptr, nullptr, nullptr};
+  long long glaunches[4] = {0, 0, 0, 0};  // kernels in each graph
+  std::vector<GraphEvent> gev[4];
 };
 
 namespace {
@@ -159,7 +172,22 @@ struct ProfScope {
   int cls;
   size_t slot = 0;
   bool on;
-  ProfScope(ctm_ctx* ctx, int k, double flops) : c(ctx), cls(k), on(ctx->prof_on) {
+  bool deferred;  // the callee records the two events around the kernel itself
+  cudaEvent_t g0 = nullptr, g1 = nullptr;  // event pair owned by a graph being captured
+  ProfScope(ctm_ctx* ctx, int k, double flops, bool defer = false)
+      : c(ctx), cls(k), on(((ctx->prof_mask >> k) & 1) != 0), deferred(defer) {
+    if (c->capturing) {
+      // tensor-core launches of a captured move carry their own event pair,
+      // recorded by every replay of the graph
+      on = false;
+      if (cls == 1 || cls == 2) {
+        if (cudaEventCreate(&g0) != cudaSuccess || cudaEventCreate(&g1) != cudaSuccess)
+          fail(CTM_ERR_CUDA, "event create");
+        c->gev[c->capture_dir].push_back({cls, g0, g1, flops});
+        if (!deferred) cudaEventRecordWithFlags(g0, c->stream, cudaEventRecordExternal);
+      }
+      return;
+    }
     if (!on) return;
     auto& pc = c->prof[cls];
     if (pc.used + 2 > pc.ev.size()) {
@@ -173,10 +201,13 @@ struct ProfScope {
     pc.used += 2;
     pc.count += 1;
     pc.flops += flops;
-    cudaEventRecord(pc.ev[slot], c->stream);
+    if (!deferred) cudaEventRecord(pc.ev[slot], c->stream);
   }
+  cudaEvent_t ev0() const { return g0 ? g0 : (on ? c->prof[cls].ev[slot] : nullptr); }
+  cudaEvent_t ev1() const { return g1 ? g1 : (on ? c->prof[cls].ev[slot + 1] : nullptr); }
   ~ProfScope() {
-    if (on) cudaEventRecord(c->prof[cls].ev[slot + 1], c->stream);
+    if (g1 && !deferred) cudaEventRecordWithFlags(g1, c->stream, cudaEventRecordExternal);
+    if (on && !deferred) cudaEventRecord(c->prof[cls].ev[slot + 1], c->stream);
   }
 };
 
@@ -360,10 +391,13 @@ Tmp ein(ctm_ctx* c, const char* spec, const Ten& A, const Ten& B) {
   if (c->precision == CTM_FP64) return ein64(c, spec, A, B);
   Plan p = make_plan(parse(spec), A, B);
   Tmp C(c, p.out_dims, p.out_nd);
-  ProfScope ps(c, c->precision == CTM_TF32 ? 1 : 2, 2.0 * p.M * p.N * p.K);
+  ProfScope ps(c, c->precision == CTM_TF32 ? 1 : 2, 2.0 * p.M * p.N * p.K, true);
   int rc = tc_contract(c->tc, c->stream, c->precision, p.M, p.N, p.K, A.p, p.Am, p.Ak, B.p,
-                       p.Bk, p.Bn, C.t.p, p.Cm, p.Cn, &c->launches, &c->flags->error);
-  if (rc != 0) fail(CTM_ERR_CUDA, std::string("tensor-core contraction failed: ") + spec);
+                       p.Bk, p.Bn, C.t.p, p.Cm, p.Cn, &c->launches, &c->flags->error, ps.ev0(),
+                       ps.ev1());
+  if (rc != 0)
+    fail(CTM_ERR_CUDA, std::string("tensor-core contraction failed (") + std::to_string(rc) + ", " +
+                           cudaGetErrorString(cudaGetLastError()) + "): " + spec);
   check_finite(c, C.t, spec);
   return C;
 }
@@ -565,9 +599,9 @@ void gemm_mixed(ctm_ctx* c, long long M, long long N, long long K, const double*
     gemm64(c, M, N, K, 1.0, A, Am, Ak, B, Bk, Bn, 0.0, C, Cm, Cn);
     return;
   }
-  ProfScope ps(c, c->precision == CTM_TF32 ? 1 : 2, 2.0 * M * N * K);
+  ProfScope ps(c, c->precision == CTM_TF32 ? 1 : 2, 2.0 * M * N * K, true);
   if (tc_contract(c->tc, c->stream, c->precision, M, N, K, A, Am, Ak, B, Bk, Bn, C, Cm, Cn,
-                  &c->launches, &c->flags->error) != 0)
+                  &c->launches, &c->flags->error, ps.ev0(), ps.ev1()) != 0)
     fail(CTM_ERR_CUDA, "tensor-core sketch product failed");
 }
 
@@ -676,7 +710,7 @@ Tmp left_svd_power(ctm_ctx* c, const double* M, int rows, int cols, int k, int s
     Tmp Y(c, {rows, k});
     gemm_mixed(c, rows, k, cols, M, lm1(rows, cols), lm1(cols, 1), Z.t.p, lm1(cols, k), lm1(k, 1),
                Y.t.p, lm1(rows, k), lm1(k, 1));
-    Q = cholqr(c, Y.t.p, k, 1, rows, k, 4);
+    Q = cholqr(c, Y.t.p, k, 1, rows, k, 3);
   }
   if (!ce.p || ce.rows != rows || ce.k != k) {
     ce.p = owned_alloc(c, (long long)rows * k);
@@ -759,19 +793,19 @@ Proj projector_standard(ctm_ctx* c, int r, int x) {
   Ten C2 = E(c, 0, 2, y, r), T3 = edge_fused(E(c, 1, 3, y, r));
   Tmp EL;
   {
-    Tmp y1 = ein64(c, "dg,gUe->dUe", C1, T2x);
-    Tmp y2 = ein64(c, "dUe,aLd->aLUe", y1, T1);
+    Tmp y1 = ein(c, "dg,gUe->dUe", C1, T2x);
+    Tmp y2 = ein(c, "dUe,aLd->aLUe", y1, T1);
     y1.release();
-    EL = ein64(c, "aLUe,ULXR->aXeR", y2, ax);
+    EL = ein(c, "aLUe,ULXR->aXeR", y2, ax);
   }
   Tmp ER;
   {
-    Tmp z1 = ein64(c, "eUz,zh->eUh", T2y, C2);
-    Tmp z2 = ein64(c, "eUh,hRb->eURb", z1, T3);
+    Tmp z1 = ein(c, "eUz,zh->eUh", T2y, C2);
+    Tmp z2 = ein(c, "eUh,hRb->eURb", z1, T3);
     z1.release();
-    ER = ein64(c, "eURb,ULYR->eLbY", z2, ay);
+    ER = ein(c, "eURb,ULYR->eLbY", z2, ay);
   }
-  Tmp Q = ein64(c, "aXeR,eRbY->aXYb", EL, ER);
+  Tmp Q = ein(c, "aXeR,eRbY->aXYb", EL, ER);
   EL.release();
   ER.release();
   const int na = Q.t.dims[0], nb = Q.t.dims[3];
@@ -799,10 +833,10 @@ void split_projector(ctm_ctx* c, const Ten& Mt, Tmp& v1, Tmp& v2, Tmp& N, int sl
   else
     v1 = left_svd(c, Mt.p, na * D, D * nb, k1);
   v1.t = view(v1.t, {na, D, k1});
-  N = ein64(c, "akc,akbz->cbz", v1, Mt);
+  N = ein(c, "akc,akbz->cbz", v1, Mt);
   const int k2 = std::min(c->chi, k1 * D);
   if (fast && k2 == nb && k2 < k1 * D)  // keeps the whole column space: any orthonormal basis
-    v2 = cholqr(c, N.t.p, nb, 1, k1 * D, nb, 4);
+    v2 = cholqr(c, N.t.p, nb, 1, k1 * D, nb, 3);
   else
     v2 = left_svd(c, N.t.p, k1 * D, nb, k2);
   v2.t = view(v2.t, {k1, D, k2});
@@ -848,22 +882,22 @@ Proj projector_seq(ctm_ctx* c, int r, int x, int col) {
   Ten T2 = E(c, 1, 2, x, r);
   Tmp vl1, vl2, Nl, vr1, vr2, Nr;
   {
-    Tmp L = ein64(c, "dg,akbd->gkba", C1, T1);
+    Tmp L = ein(c, "dg,akbd->gkba", C1, T1);
     split_projector(c, L, vl1, vl2, Nl, base + 0);
   }
   {
-    Tmp R = ein64(c, "ez,zkbw->ekbw", C2, T3);
+    Tmp R = ein(c, "ez,zkbw->ekbw", C2, T3);
     split_projector(c, R, vr1, vr2, Nr, base + 1);
   }
-  Tmp C1p = ein64(c, "cby,cba->ya", vl2, Nl);
-  Tmp C2p = ein64(c, "cby,cbw->yw", vr2, Nr);
+  Tmp C1p = ein(c, "cby,cba->ya", vl2, Nl);
+  Tmp C2p = ein(c, "cby,cbw->yw", vr2, Nr);
   Nl.release();
   Nr.release();
   // T'2: the top edge with x absorbed, left bond by v_l, right bond by v_r
   Tmp T2p = absorb_edge_seq(c, T2, S, "ipon", vl1, vl2, vr1, vr2);
-  Tmp Xm = ein64(c, "ya,ykbz->akbz", C1p, T2p);
+  Tmp Xm = ein(c, "ya,ykbz->akbz", C1p, T2p);
   T2p.release();
-  Tmp M = ein64(c, "akbz,zw->akbw", Xm, C2p);
+  Tmp M = ein(c, "akbz,zw->akbw", Xm, C2p);
   Xm.release();
   Proj P;
   Tmp N;
@@ -929,10 +963,107 @@ void check_flags(ctm_ctx* c) {
   }
 }
 
+bool all_bonds_at(ctm_ctx* c, int target);
+
+// After a replay of the graph of direction dir: add its tensor-core event pairs
+// to the per-class timing when that class is being timed.
+void graph_account(ctm_ctx* c, int dir) {
+  if (!c->prof_mask) return;
+  ck(cudaStreamSynchronize(c->stream), "sync");
+  for (const auto& g : c->gev[dir]) {
+    if (!((c->prof_mask >> g.cls) & 1)) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, g.e0, g.e1) == cudaSuccess) c->prof[g.cls].ms += ms;
+    c->prof[g.cls].count += 1;
+    c->prof[g.cls].flops += g.flops;
+  }
+  cudaGetLastError();
+}
+
+void drop_graphs(ctm_ctx* c) {
+  for (int d = 0; d < 4; ++d) {
+    if (c->gexec[d]) cudaGraphExecDestroy(c->gexec[d]);
+    c->gexec[d] = nullptr;
+    for (auto& g : c->gev[d]) {
+      cudaEventDestroy(g.e0);
+      cudaEventDestroy(g.e1);
+    }
+    c->gev[d].clear();
+    c->warm[d] = false;
+  }
+}
+
+bool graph_eligible(ctm_ctx* c, int mode) {
+  static int off = -1;
+  if (off < 0) {
+    const char* e = std::getenv("CTM_NO_GRAPHS");
+    off = (e && *e && *e != '0') ? 1 : 0;
+  }
+  return !off && c->graphs_ok && c->stream != nullptr && c->precision != CTM_FP64 &&
+         mode == CTM_REDUCED_SEQUENTIAL && !trace_on() && !check_on() && all_bonds_at(c, c->chi);
+}
+
+// A steady-state move is a fixed launch sequence: once a direction has run
+// eagerly with warm caches, its two column absorptions are captured into a
+// CUDA graph and replayed (every updated tensor flips its ping-pong buffer
+// twice per move, so the buffers a graph reads and writes stay the same).
 void do_move(ctm_ctx* c, int dir, int mode) {
+  if (graph_eligible(c, mode)) {
+    if (!c->gexec[dir] && c->warm[dir]) {
+      cudaGraph_t graph = nullptr;
+      bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        c->capturing = true;
+        c->capture_dir = dir;
+        std::string why;
+        const long long l0 = c->launches;
+        try {
+          column_absorb(c, dir, mode, 0);
+          column_absorb(c, dir, mode, 1);
+          c->glaunches[dir] = c->launches - l0;
+          c->launches = l0;  // counted when the graph runs
+        } catch (const CtmError& e) {
+          ok = false;
+          why = e.msg;
+        }
+        c->capturing = false;
+        cudaError_t ee = cudaStreamEndCapture(c->stream, &graph);
+        if (ee != cudaSuccess) {
+          ok = false;
+          why += std::string(" end capture: ") + cudaGetErrorString(ee);
+        }
+        if (ok) {
+          ee = cudaGraphInstantiate(&c->gexec[dir], graph, 0);
+          if (ee != cudaSuccess) {
+            c->gexec[dir] = nullptr;
+            ok = false;
+            why += std::string(" instantiate: ") + cudaGetErrorString(ee);
+          }
+        }
+        if (graph) cudaGraphDestroy(graph);
+        if (!ok && std::getenv("CTM_GRAPH_DEBUG"))
+          std::fprintf(stderr, "[ctm] graph capture of direction %d failed: %s\n", dir,
+                       why.c_str());
+      }
+      cudaGetLastError();
+      if (!ok) {  // capture not possible here: run eagerly from now on
+        c->graphs_ok = false;
+        drop_graphs(c);
+      }
+    }
+    if (c->gexec[dir]) {
+      if (std::getenv("CTM_GRAPH_DEBUG")) std::fprintf(stderr, "[ctm] replay graph %d\n", dir);
+      ck(cudaGraphLaunch(c->gexec[dir], c->stream), "graph launch");
+      c->launches += c->glaunches[dir];
+      graph_account(c, dir);
+      check_flags(c);
+      return;
+    }
+  }
   column_absorb(c, dir, mode, 0);
   column_absorb(c, dir, mode, 1);
   check_flags(c);
+  if (graph_eligible(c, mode)) c->warm[dir] = true;
 }
 
 bool all_bonds_at(ctm_ctx* c, int target) {
@@ -1009,7 +1140,12 @@ std::vector<double> spectrum(ctm_ctx* c, const Ten& C) {
     ck(cudaMemcpyAsync(X.t.p, C.p, sizeof(double) * C.size(), cudaMemcpyDeviceToDevice, c->stream),
        "copy");
   }
-  jacobi(c, X.t.p, nrows, ncols, nullptr);
+  {
+    ProfScope ps(c, 3, 0.0);
+    if (jacobi_batched(c->stream, X.t.p, nrows, ncols, 1, 0, c->flags, kMaxSweeps, &c->launches,
+                       kValuesOnlyTol) != 0)
+      fail(CTM_ERR_CUDA, "Jacobi launch failed");
+  }
   Tmp sig(c, {ncols});
   int* perm = (int*)dalloc(c, (ncols + 1) / 2 + 1);
   ck(column_norms_sorted(c->stream, X.t.p, nrows, ncols, sig.t.p, perm), "norms");
@@ -1030,6 +1166,76 @@ std::vector<double> spectrum(ctm_ctx* c, const Ten& C) {
   const double nrm = std::sqrt(ss);
   if (!(nrm > 0.0)) fail(CTM_ERR_NAN, "zero corner");
   for (double& v : out) v /= nrm;
+  return out;
+}
+
+// Spectra of all 8 corners; one batched Jacobi launch when they share a shape.
+std::vector<std::vector<double>> spectra_all(ctm_ctx* c) {
+  std::vector<std::vector<double>> out;
+  const Ten& c0 = c->env[0][0][0];
+  bool same = true;
+  for (int i = 1; i < 8; ++i) {
+    const Ten& t = c->env[0][i / 2][i % 2];
+    same = same && t.dims[0] == c0.dims[0] && t.dims[1] == c0.dims[1];
+  }
+  if (!same) {
+    for (int i = 0; i < 8; ++i) out.push_back(spectrum(c, c->env[0][i / 2][i % 2]));
+    return out;
+  }
+  const int n1 = c0.dims[0], n2 = c0.dims[1];
+  const bool cols_side = n2 <= n1;
+  const int nrows = cols_side ? n1 : n2, ncols = cols_side ? n2 : n1;
+  const long long per = (long long)n1 * n2;
+  Tmp X(c, {8, ncols, nrows});
+  for (int i = 0; i < 8; ++i) {
+    const Ten& C = c->env[0][i / 2][i % 2];
+    if (cols_side) {
+      LegMap m;
+      push(m, n2, 1);
+      push(m, n1, n2);
+      ck(permute_f64(c->stream, X.t.p + i * per, C.p, m), "transpose");
+      ++c->launches;
+    } else {
+      ck(cudaMemcpyAsync(X.t.p + i * per, C.p, sizeof(double) * per, cudaMemcpyDeviceToDevice,
+                         c->stream),
+         "copy");
+    }
+  }
+  {
+    ProfScope ps(c, 3, 0.0);
+    if (jacobi_batched(c->stream, X.t.p, nrows, ncols, 8, per, c->flags, kMaxSweeps,
+                       &c->launches, kValuesOnlyTol) != 0)
+      fail(CTM_ERR_CUDA, "Jacobi launch failed");
+  }
+  Tmp sig(c, {8, ncols});
+  int* perm = (int*)dalloc(c, 4 * ncols + 1);
+  for (int i = 0; i < 8; ++i) {
+    ck(column_norms_sorted(c->stream, X.t.p + i * per, nrows, ncols, sig.t.p + i * ncols,
+                           perm + i * ncols),
+       "norms");
+    c->launches += 2;
+  }
+  std::vector<double> hs(8 * ncols);
+  std::vector<int> hp(8 * ncols);
+  ck(cudaMemcpyAsync(hs.data(), sig.t.p, sizeof(double) * 8 * ncols, cudaMemcpyDeviceToHost,
+                     c->stream),
+     "d2h");
+  ck(cudaMemcpyAsync(hp.data(), perm, sizeof(int) * 8 * ncols, cudaMemcpyDeviceToHost, c->stream),
+     "d2h");
+  dfree(c, perm);
+  check_flags(c);
+  for (int i = 0; i < 8; ++i) {
+    std::vector<double> v(ncols);
+    double ss = 0.0;
+    for (int j = 0; j < ncols; ++j) {
+      v[j] = hs[i * ncols + hp[i * ncols + j]];
+      ss += v[j] * v[j];
+    }
+    const double nrm = std::sqrt(ss);
+    if (!(nrm > 0.0)) fail(CTM_ERR_NAN, "zero corner");
+    for (double& x : v) x /= nrm;
+    out.push_back(std::move(v));
+  }
   return out;
 }
 
@@ -1252,15 +1458,15 @@ int ctm_converge(ctm_ctx* c, int mode, int max_iter, double tol, int* iters_done
     return CTM_ERR_ARG;
   bool converged = false;
   int rc = guarded(c, [&] {
-    std::vector<std::vector<double>> old;
-    for (int i = 0; i < 8; ++i) old.push_back(spectrum(c, c->env[0][i / 2][i % 2]));
+    std::vector<std::vector<double>> old = spectra_all(c);
     double delta = INFINITY;
     int it = 0;
     for (it = 1; it <= max_iter; ++it) {
       for (int dir = 0; dir < 4; ++dir) do_move(c, dir, mode);
       delta = 0.0;
+      std::vector<std::vector<double>> all = spectra_all(c);
       for (int i = 0; i < 8; ++i) {
-        std::vector<double> s = spectrum(c, c->env[0][i / 2][i % 2]);
+        std::vector<double>& s = all[i];
         const size_t n = std::max(s.size(), old[i].size());
         double acc = 0.0;
         for (size_t j = 0; j < n; ++j) {
@@ -1299,6 +1505,18 @@ int ctm_corner_spectrum(ctm_ctx* c, int corner, double* s, int* len) {
   });
 }
 
+int ctm_corner_spectra(ctm_ctx* c, double* s, int maxlen, int* lens) {
+  if (!c || !s || !lens || maxlen < 1) return CTM_ERR_ARG;
+  return guarded(c, [&] {
+    std::vector<std::vector<double>> all = spectra_all(c);
+    for (int i = 0; i < 8; ++i) {
+      const int n = std::min((int)all[i].size(), maxlen);
+      for (int j = 0; j < n; ++j) s[(long long)i * maxlen + j] = all[i][j];
+      lens[i] = n;
+    }
+  });
+}
+
 int ctm_log_kappa(ctm_ctx* c, double* value) {
   if (!c || !value) return CTM_ERR_ARG;
   return guarded(c, [&] { *value = log_kappa(c); });
@@ -1325,6 +1543,7 @@ int ctm_set_tensor(ctm_ctx* c, int kind, int k, int x, const double* in, const i
   if (dims[0] < 1 || dims[0] > cmax || dims[nd - 1] < 1 || dims[nd - 1] > cmax) return CTM_ERR_ARG;
   if (nd == 4 && (dims[1] != c->D || dims[2] != c->D)) return CTM_ERR_ARG;
   return guarded(c, [&] {
+    drop_graphs(c);  // recorded graphs assume the current shapes and buffers
     Ten& t = c->env[kind][k - 1][x];
     t.nd = nd;
     for (int i = 0; i < nd; ++i) t.dims[i] = dims[i];
@@ -1381,7 +1600,7 @@ int ctm_contract_test(int precision, long long M, long long N, long long K, cons
         break;
       }
       if (tc_contract(tc, 0, precision, M, N, K, dA, Am, Ak, dB, Bk, Bn, dC, Cm, Cn, &launches,
-                      nullptr) != 0) {
+                      nullptr, nullptr, nullptr) != 0) {
         bail(CTM_ERR_CUDA);
         break;
       }
@@ -1410,7 +1629,7 @@ int ctm_profile_enable(ctm_ctx* c, int on) {
       pc.count = 0;
       pc.ms = pc.flops = 0.0;
     }
-    c->prof_on = on != 0;
+    c->prof_mask = on & 0xF;
   });
 }
 
@@ -1430,6 +1649,7 @@ void ctm_free(ctm_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   for (void* p : c->owned) cudaFree(p);
+  drop_graphs(c);
   if (c->tc) tc_destroy(c->tc);
   for (auto& pc : c->prof)
     for (cudaEvent_t e : pc.ev) cudaEventDestroy(e);

@@ -90,6 +90,14 @@ cudaError_t gaussian_fill(cudaStream_t s, double* x, long long n, unsigned long 
 int jacobi_onesided(cudaStream_t s, double* X, int nrows, int ncols, double* V,
                     DevFlags* flags, int max_sweeps, long long* launches);
 
+// nprob independent problems X + p * pstride in one launch (no accumulation).
+// tol_override > 0 replaces the cosine tolerance sqrt(nrows) * eps; singular
+// values alone converge quadratically in the cosines, so 1e-10 already gives
+// them to FP64 accuracy.
+int jacobi_batched(cudaStream_t s, double* X, int nrows, int ncols, int nprob, long long pstride,
+                   DevFlags* flags, int max_sweeps, long long* launches, double tol_override);
+constexpr double kValuesOnlyTol = 1e-10;
+
 // Column norms of X (nrows x ncols col-major) into sig[ncols]; perm[r] = index of
 // the r-th largest.  Single-block kernels.
 cudaError_t column_norms_sorted(cudaStream_t s, const double* X, int nrows, int ncols,

@@ -21,31 +21,42 @@ static_assert(offsetof(DevFlags, error) == kDevFlagsResetBytes, "DevFlags layout
 // Bounded grid barrier for cooperative launches.  Every wait has an iteration
 // cap; on timeout the kernel records an error and all blocks return.
 // ---------------------------------------------------------------------------
-constexpr long long kBarrierSpinLimit = 1ll << 24;  // x ~64 ns sleeps: about a second
+constexpr long long kBarrierCycleLimit = 4000000000ll;  // ~2 s of SM clock
 
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned atom_add_release_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
+               : "memory");
+  return old;
+}
+
+// Sense-by-generation grid barrier: one release-add per block, the last block
+// resets the counter and bumps the generation, the others poll the generation
+// with acquire loads.  The poll gives up after kBarrierCycleLimit clocks.
 __device__ __forceinline__ bool grid_barrier(DevFlags* fl, unsigned nblocks) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = &fl->bar_gen;
-    const unsigned g = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&fl->bar_count, 1u);
+    const unsigned g = ld_acquire_u32(&fl->bar_gen);
+    const unsigned arrived = atom_add_release_u32(&fl->bar_count, 1u);
     if (arrived == nblocks - 1) {
       atomicExch(&fl->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&fl->bar_gen, 1u);
+      atom_add_release_u32(&fl->bar_gen, 1u);
     } else {
-      long long spins = 0;
-      while (*gen == g) {
-        if (++spins > kBarrierSpinLimit) {
+      const long long t0 = clock64();
+      while (ld_acquire_u32(&fl->bar_gen) == g) {
+        if (clock64() - t0 > kBarrierCycleLimit) {
           atomicExch(&fl->error, 1);
           break;
         }
-        __nanosleep(64);
       }
     }
-    __threadfence();
     s_ok = (*(volatile int*)&fl->error) == 0;
   }
   __syncthreads();
@@ -84,18 +95,20 @@ __device__ __forceinline__ int rr_col(int p, int s, int n) {
 }
 
 __global__ void __launch_bounds__(kJacobiThreads)
-jacobi_kernel(double* __restrict__ X, int nrows, int ncols, int npad, double* __restrict__ V,
-              DevFlags* fl, int max_sweeps, double tol) {
+jacobi_kernel(double* __restrict__ Xall, int nrows, int ncols, int npad, double* __restrict__ V,
+              DevFlags* fl, int max_sweeps, double tol, int nprob, long long pstride) {
   const unsigned nblocks = gridDim.x;
   const int npairs = npad / 2;
+  double* X = Xall;
   // columns whose squared norm is below 1e-32 ||X||_F^2 lie under FP64
   // resolution: they are still rotated but do not count for convergence
   {
     double part = 0.0, z1 = 0.0, z2 = 0.0;
-    const long long total = (long long)nrows * ncols;
-    for (long long e = blockIdx.x * (long long)kJacobiThreads + threadIdx.x; e < total;
-         e += (long long)gridDim.x * kJacobiThreads)
-      part = fma(X[e], X[e], part);
+    const long long per = (long long)nrows * ncols;
+    for (int p = 0; p < nprob; ++p)
+      for (long long e = blockIdx.x * (long long)kJacobiThreads + threadIdx.x; e < per;
+           e += (long long)gridDim.x * kJacobiThreads)
+        part = fma(Xall[p * pstride + e], Xall[p * pstride + e], part);
     block_sum3<kJacobiThreads>(part, z1, z2);
     if (threadIdx.x == 0 && part > 0.0) atomicAdd(&fl->fro2, part);
     if (!grid_barrier(fl, nblocks)) return;
@@ -104,7 +117,9 @@ jacobi_kernel(double* __restrict__ X, int nrows, int ncols, int npad, double* __
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     double local_max = 0.0;
     for (int step = 0; step < npad - 1; ++step) {
-      for (int k = blockIdx.x; k < npairs; k += gridDim.x) {
+      for (int kk = blockIdx.x; kk < npairs * nprob; kk += gridDim.x) {
+        const int k = kk % npairs;
+        X = Xall + (long long)(kk / npairs) * pstride;
         int i = rr_col(k, step, npad);
         int j = rr_col(npad - 1 - k, step, npad);
         if (i >= ncols || j >= ncols) continue;
@@ -184,8 +199,12 @@ cudaError_t fill_identity(cudaStream_t s, double* x, int n) {
   return cudaGetLastError();
 }
 
+int jacobi_batched(cudaStream_t s, double* X, int nrows, int ncols, int nprob, long long pstride,
+                   DevFlags* flags, int max_sweeps, long long* launches, double tol_override);
+
 int jacobi_onesided(cudaStream_t s, double* X, int nrows, int ncols, double* V, DevFlags* flags,
                     int max_sweeps, long long* launches) {
+  if (!V) return jacobi_batched(s, X, nrows, ncols, 1, 0, flags, max_sweeps, launches, 0.0);
   if (ncols < 2) {
     if (V && ncols == 1) {
       if (fill_identity(s, V, 1) != cudaSuccess) return -3;
@@ -204,10 +223,41 @@ int jacobi_onesided(cudaStream_t s, double* X, int nrows, int ncols, double* V, 
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, kJacobiThreads, 0);
   if (per_sm < 1) return -3;
   int grid = npad / 2;
-  if (grid > nsm * per_sm) grid = nsm * per_sm;
+  if (grid > nsm) grid = nsm;  // one block per SM: fewer arrivals per barrier
   if (cudaMemsetAsync(flags, 0, kDevFlagsResetBytes, s) != cudaSuccess) return -3;
   const double tol = 2.220446049250313e-16 * std::sqrt((double)(nrows > 1 ? nrows : 1));
-  void* args[] = {&X, &nrows, &ncols, (void*)&npad, &V, &flags, &max_sweeps, (void*)&tol};
+  int nprob = 1;
+  long long pstride = 0;
+  void* args[] = {&X, &nrows, &ncols, (void*)&npad, &V, &flags, &max_sweeps, (void*)&tol,
+                  &nprob, &pstride};
+  if (cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(grid), dim3(kJacobiThreads), args,
+                                  0, s) != cudaSuccess)
+    return -3;
+  ++*launches;
+  return 0;
+}
+
+// nprob independent problems X + p * pstride (same shape, no rotation
+// accumulation) in one cooperative launch: one grid barrier per round-robin
+// step serves all of them.
+int jacobi_batched(cudaStream_t s, double* X, int nrows, int ncols, int nprob, long long pstride,
+                   DevFlags* flags, int max_sweeps, long long* launches, double tol_override) {
+  if (ncols < 2 || nprob < 1) return 0;
+  const int npad = ncols + (ncols & 1);
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, kJacobiThreads, 0);
+  if (per_sm < 1) return -3;
+  long long want = (long long)(npad / 2) * nprob;
+  int grid = (int)(want < (long long)nsm ? want : (long long)nsm);  // one block per SM
+  if (cudaMemsetAsync(flags, 0, kDevFlagsResetBytes, s) != cudaSuccess) return -3;
+  const double tol = tol_override > 0.0
+                         ? tol_override
+                         : 2.220446049250313e-16 * std::sqrt((double)(nrows > 1 ? nrows : 1));
+  double* V = nullptr;
+  void* args[] = {&X, &nrows, &ncols, (void*)&npad, &V, &flags, &max_sweeps, (void*)&tol,
+                  &nprob, &pstride};
   if (cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(grid), dim3(kJacobiThreads), args,
                                   0, s) != cudaSuccess)
     return -3;

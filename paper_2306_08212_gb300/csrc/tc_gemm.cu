@@ -346,6 +346,16 @@ int tc_error(TcGemm* t, cudaStream_t s) {
 
 namespace {
 
+// Inside a stream capture an event record must become an external event node
+// to be replayed; outside a capture it is a plain record.
+void record(cudaEvent_t ev, cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(ev, s);
+}
+
 bool make_map(TcGemm* t, CUtensorMap* map, void* base, bool tf32, long long rows, long long Kp,
               int box_rows) {
   const cuuint64_t gdim[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
@@ -391,7 +401,8 @@ cudaError_t pack(cudaStream_t s, void* out, const double* in, const LegMap& Rm, 
 int tc_contract(TcGemm* t, cudaStream_t s, int precision, long long M, long long N, long long K,
                 const double* A, const LegMap& Am, const LegMap& Ak, const double* B,
                 const LegMap& Bk, const LegMap& Bn, double* C, const LegMap& Cm,
-                const LegMap& Cn, long long* launches, int* err_word) {
+                const LegMap& Cn, long long* launches, int* err_word, cudaEvent_t ev_begin,
+                cudaEvent_t ev_end) {
   if (!t) return -6;
   int* err = err_word ? err_word : t->err;
   if (M <= 0 || N <= 0) return 0;
@@ -420,6 +431,7 @@ int tc_contract(TcGemm* t, cudaStream_t s, int precision, long long M, long long
     rc = -3;
   } else {
     const int nk = (int)((Kp + (tf32 ? 32 : 64) - 1) / (tf32 ? 32 : 64));
+    if (ev_begin) record(ev_begin, s);
     if (tf32) {
       e = BN == 64    ? launch<64, true>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err)
           : BN == 128 ? launch<128, true>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err)
@@ -429,8 +441,13 @@ int tc_contract(TcGemm* t, cudaStream_t s, int precision, long long M, long long
           : BN == 128 ? launch<128, false>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err)
                       : launch<256, false>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err);
     }
+    if (ev_end) record(ev_end, s);
     ++*launches;
     if (e != cudaSuccess) rc = -3;
+  }
+  if (rc != 0 && ev_begin && ev_end) {  // keep the event pair well-formed
+    record(ev_begin, s);
+    record(ev_end, s);
   }
   cudaFreeAsync(pa, s);
   cudaFreeAsync(pb, s);

@@ -36,6 +36,7 @@ SIGNATURES = {
     "ctm_converge": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double, _I, _D]),
     "ctm_expect_bond": (ctypes.c_int, [_P, ctypes.c_int, _D, _D]),
     "ctm_corner_spectrum": (ctypes.c_int, [_P, ctypes.c_int, _D, _I]),
+    "ctm_corner_spectra": (ctypes.c_int, [_P, _D, ctypes.c_int, _I]),
     "ctm_log_kappa": (ctypes.c_int, [_P, _D]),
     "ctm_get_tensor": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _I]),
     "ctm_set_tensor": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _I]),
@@ -142,6 +143,13 @@ def ctm_corner_spectrum(ctx, corner, maxlen):
     return rc, s[: n.value]
 
 
+def ctm_corner_spectra(ctx, maxlen):
+    s = np.zeros((8, maxlen))
+    lens = (ctypes.c_int * 8)()
+    rc = load().ctm_corner_spectra(ctx, _dptr(s), int(maxlen), lens)
+    return rc, [s[i, : lens[i]] for i in range(8)]
+
+
 def ctm_log_kappa(ctx):
     v = ctypes.c_double(0.0)
     rc = load().ctm_log_kappa(ctx, ctypes.byref(v))
@@ -173,8 +181,9 @@ def ctm_kernel_launches(ctx):
 PROFILE_CLASSES = {0: "gemm_f64", 1: "tc_tf32_gemm", 2: "tc_bf16_gemm", 3: "jacobi_f64"}
 
 
-def ctm_profile_enable(ctx, on=True):
-    return load().ctm_profile_enable(ctx, int(bool(on)))
+def ctm_profile_enable(ctx, mask=0xF):
+    """Time the kernel classes whose bit (1 << class) is set; 0 stops."""
+    return load().ctm_profile_enable(ctx, int(mask))
 
 
 def ctm_profile_read(ctx, cls):
@@ -185,9 +194,9 @@ def ctm_profile_read(ctx, cls):
     return rc, n.value, ms.value, fl.value
 
 
-def ctm_kernel_stats_reset(ctx):
+def ctm_kernel_stats_reset(ctx, mask=0xF):
     """Clear and start the per-class CUDA-event kernel timing."""
-    rc = ctm_profile_enable(ctx, True)
+    rc = ctm_profile_enable(ctx, mask)
     if rc != OK:
         raise CtmError(rc, ctm_last_error(ctx))
 
@@ -274,7 +283,9 @@ class Env:
         return s
 
     def corner_spectra(self):
-        return [self.corner_spectrum(i) for i in range(8)]
+        rc, out = ctm_corner_spectra(self.ctx, max(self.chi, 1) * 4 + 16)
+        self._check(rc)
+        return out
 
     def log_kappa(self):
         rc, v = ctm_log_kappa(self.ctx)

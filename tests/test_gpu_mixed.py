@@ -45,3 +45,27 @@ def test_mixed_precision_error_vs_fp64(ctm, prec):
     print(f"{prec}: max |dE_bond| = {de:.3e}, max |ds| (top 16) = {ds:.3e}")
     assert de < BOUND[prec]
     assert ds < BOUND[prec]
+
+
+def test_graph_replay_matches_eager(ctm):
+    """Steady-state moves replayed from CUDA graphs (context on a side stream)
+    give the same results as eager execution (context on the default stream)."""
+    import torch
+    A, B = I.random_sites(2, 4, 2)
+    H = O.heisenberg_bond()
+    res = []
+    for use_side in (False, True):
+        stream = torch.cuda.Stream() if use_side else torch.cuda.default_stream()
+        with torch.cuda.stream(stream):
+            g = ctm.Env(A, B, 64, precision="tf32")
+            try:
+                for _ in range(3):
+                    for d in O.MOVE_ORDER:
+                        g.move(d, "reduced_sequential")
+                res.append(([g.expect_bond(b, H) for b in range(4)], g.corner_spectra()))
+            finally:
+                g.free()
+    (e0, s0), (e1, s1) = res
+    np.testing.assert_allclose(e1, e0, rtol=0, atol=1e-12)
+    for a, b in zip(s0, s1):
+        np.testing.assert_allclose(b, a, rtol=0, atol=1e-12)
