@@ -76,6 +76,9 @@ struct ctm_ctx {
     cudaEvent_t e0, e1;
     double flops;
   };
+  cudaStream_t side[3] = {nullptr, nullptr, nullptr};  // for independent factorisations
+  std::vector<cudaEvent_t> fork_events;
+  size_t fork_next = 0;
   bool graphs_ok = true;
   bool capturing = false;
   int capture_dir = -1;
@@ -752,6 +755,28 @@ void commit(ctm_ctx* c, int kind, int k, int x, int r, const Ten& src) {
 // ---------------------------------------------------------------------------
 // Moves
 // ---------------------------------------------------------------------------
+// Independent factorisations run on side streams in the mixed-precision path
+// (their FP64 Cholesky chains are latency-bound, so overlapping them pays).
+// The host issues the branches one after the other, switching c->stream; in a
+// stream capture the event edges become graph dependencies.
+bool can_fork(ctm_ctx* c) { return c->precision != CTM_FP64 && c->side[0] != nullptr; }
+
+cudaEvent_t fork_event(ctm_ctx* c) {
+  if (c->fork_next == c->fork_events.size()) {
+    cudaEvent_t e;
+    ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    c->fork_events.push_back(e);
+  }
+  return c->fork_events[c->fork_next++];
+}
+
+// Make `to` wait for the work issued so far on `from`.
+void stream_dep(ctm_ctx* c, cudaStream_t from, cudaStream_t to) {
+  cudaEvent_t e = fork_event(c);
+  ck(cudaEventRecord(e, from), "record");
+  ck(cudaStreamWaitEvent(to, e, 0), "wait");
+}
+
 struct Proj {  // 4-index (standard) or split (sequential) isometry of one bond
   Tmp v;       // standard: [chi, D, D, k]
   Tmp v1, v2;  // sequential: [chi, D, c], [c, D, k]
@@ -881,14 +906,22 @@ Proj projector_seq(ctm_ctx* c, int r, int x, int col) {
   Ten C2 = E(c, 0, 2, x, r), T3 = E(c, 1, 3, x, r);
   Ten T2 = E(c, 1, 2, x, r);
   Tmp vl1, vl2, Nl, vr1, vr2, Nr;
+  const cudaStream_t main = c->stream;
+  const bool fork = can_fork(c);
+  // P_a: L on the caller's stream, R on side 0; P_b (on side 1): R on side 2
+  cudaStream_t sideR = fork ? c->side[x == 0 ? 0 : 2] : main;
+  if (fork) stream_dep(c, main, sideR);
   {
     Tmp L = ein(c, "dg,akbd->gkba", C1, T1);
     split_projector(c, L, vl1, vl2, Nl, base + 0);
   }
+  c->stream = sideR;
   {
     Tmp R = ein(c, "ez,zkbw->ekbw", C2, T3);
     split_projector(c, R, vr1, vr2, Nr, base + 1);
   }
+  c->stream = main;
+  if (fork) stream_dep(c, sideR, main);
   Tmp C1p = ein(c, "cby,cba->ya", vl2, Nl);
   Tmp C2p = ein(c, "cby,cbw->yw", vr2, Nr);
   Nl.release();
@@ -908,8 +941,20 @@ Proj projector_seq(ctm_ctx* c, int r, int x, int col) {
 // One column absorption in frame r (Sec. II, Fig. 2a-b).
 void column_absorb(ctm_ctx* c, int r, int mode, int col) {
   Proj P[2];
-  for (int x = 0; x < 2; ++x)
-    P[x] = (mode == CTM_STANDARD) ? projector_standard(c, r, x) : projector_seq(c, r, x, col);
+  const cudaStream_t main = c->stream;
+  const bool fork = mode == CTM_REDUCED_SEQUENTIAL && can_fork(c);
+  if (fork) {
+    // the two projectors are independent: P_b on side stream 1
+    stream_dep(c, main, c->side[1]);
+    P[0] = projector_seq(c, r, 0, col);
+    c->stream = c->side[1];
+    P[1] = projector_seq(c, r, 1, col);
+    c->stream = main;
+    stream_dep(c, c->side[1], main);
+  } else {
+    for (int x = 0; x < 2; ++x)
+      P[x] = (mode == CTM_STANDARD) ? projector_standard(c, r, x) : projector_seq(c, r, x, col);
+  }
   Tmp newT[2], newC1[2], newC4[2];
   for (int x = 0; x < 2; ++x) {
     const int y = other(x);
@@ -1008,6 +1053,7 @@ bool graph_eligible(ctm_ctx* c, int mode) {
 // CUDA graph and replayed (every updated tensor flips its ping-pong buffer
 // twice per move, so the buffers a graph reads and writes stay the same).
 void do_move(ctm_ctx* c, int dir, int mode) {
+  c->fork_next = 0;
   if (graph_eligible(c, mode)) {
     if (!c->gexec[dir] && c->warm[dir]) {
       cudaGraph_t graph = nullptr;
@@ -1401,6 +1447,7 @@ int ctm_init_env(ctm_ctx** out, const double* A, const double* B, int d, int D, 
     if (precision != CTM_FP64) {
       c->tc = tc_create();
       if (!c->tc) fail(CTM_ERR_UNSUPPORTED, "tensor-core GEMM unavailable");
+      for (auto& st : c->side) ck(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking), "stream");
     }
     const long long ns = (long long)d * D * D * D * D;
     for (int r = 0; r < 4; ++r)
@@ -1650,6 +1697,9 @@ void ctm_free(ctm_ctx* c) {
   cudaStreamSynchronize(c->stream);
   for (void* p : c->owned) cudaFree(p);
   drop_graphs(c);
+  for (auto& st : c->side)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t e : c->fork_events) cudaEventDestroy(e);
   if (c->tc) tc_destroy(c->tc);
   for (auto& pc : c->prof)
     for (cudaEvent_t e : pc.ev) cudaEventDestroy(e);

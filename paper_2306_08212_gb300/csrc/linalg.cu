@@ -96,12 +96,15 @@ __device__ __forceinline__ int rr_col(int p, int s, int n) {
 
 __global__ void __launch_bounds__(kJacobiThreads)
 jacobi_kernel(double* __restrict__ Xall, int nrows, int ncols, int npad, double* __restrict__ V,
-              DevFlags* fl, int max_sweeps, double tol, int nprob, long long pstride) {
+              DevFlags* fl, int max_sweeps, double tol, int nprob, long long pstride,
+              double tiny_rel) {
   const unsigned nblocks = gridDim.x;
   const int npairs = npad / 2;
   double* X = Xall;
-  // columns whose squared norm is below 1e-32 ||X||_F^2 lie under FP64
-  // resolution: they are still rotated but do not count for convergence
+  // columns whose squared norm is below tiny_rel ||X||_F^2 lie under the
+  // resolution that matters (1e-32: FP64; 1e-24 when only singular values
+  // above 1e-12 of the largest are wanted): they are still rotated but do not
+  // count for convergence
   {
     double part = 0.0, z1 = 0.0, z2 = 0.0;
     const long long per = (long long)nrows * ncols;
@@ -113,7 +116,7 @@ jacobi_kernel(double* __restrict__ Xall, int nrows, int ncols, int npad, double*
     if (threadIdx.x == 0 && part > 0.0) atomicAdd(&fl->fro2, part);
     if (!grid_barrier(fl, nblocks)) return;
   }
-  const double tiny = 1e-32 * (*(volatile double*)&fl->fro2);
+  const double tiny = tiny_rel * (*(volatile double*)&fl->fro2);
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     double local_max = 0.0;
     for (int step = 0; step < npad - 1; ++step) {
@@ -184,6 +187,95 @@ jacobi_kernel(double* __restrict__ Xall, int nrows, int ncols, int npad, double*
   }
 }
 
+// Values-only variant: one warp per column pair (eight pairs per block in
+// flight), warp-shuffle reductions, so the FP64 latency of several pairs
+// overlaps within a step.  Same rotation, ordering and stopping rule.
+__global__ void __launch_bounds__(kJacobiThreads)
+jacobi_warp_kernel(double* __restrict__ Xall, int nrows, int ncols, int npad, DevFlags* fl,
+                   int max_sweeps, double tol, int nprob, long long pstride, double tiny_rel) {
+  const unsigned nblocks = gridDim.x;
+  const int npairs = npad / 2;
+  const int lane = threadIdx.x % 32;
+  const int gwarp = blockIdx.x * (kJacobiThreads / 32) + threadIdx.x / 32;
+  const int nwarps = gridDim.x * (kJacobiThreads / 32);
+  {
+    double part = 0.0, z1 = 0.0, z2 = 0.0;
+    const long long per = (long long)nrows * ncols;
+    for (int p = 0; p < nprob; ++p)
+      for (long long e = blockIdx.x * (long long)kJacobiThreads + threadIdx.x; e < per;
+           e += (long long)gridDim.x * kJacobiThreads)
+        part = fma(Xall[p * pstride + e], Xall[p * pstride + e], part);
+    block_sum3<kJacobiThreads>(part, z1, z2);
+    if (threadIdx.x == 0 && part > 0.0) atomicAdd(&fl->fro2, part);
+    if (!grid_barrier(fl, nblocks)) return;
+  }
+  const double tiny = tiny_rel * (*(volatile double*)&fl->fro2);
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double local_max = 0.0;
+    for (int step = 0; step < npad - 1; ++step) {
+      for (int kk = gwarp; kk < npairs * nprob; kk += nwarps) {
+        const int k = kk % npairs;
+        double* X = Xall + (long long)(kk / npairs) * pstride;
+        int i = rr_col(k, step, npad);
+        int j = rr_col(npad - 1 - k, step, npad);
+        if (i >= ncols || j >= ncols) continue;
+        double* xi = X + (long long)i * nrows;
+        double* xj = X + (long long)j * nrows;
+        double a = 0.0, b = 0.0, g = 0.0;
+        for (int r = lane; r < nrows; r += 32) {
+          const double u = xi[r], v = xj[r];
+          a = fma(u, u, a);
+          b = fma(v, v, b);
+          g = fma(u, v, g);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        if (!(a > 0.0) || !(b > 0.0)) continue;
+        const double cosang = fabs(g) / (sqrt(a) * sqrt(b));
+        if (a > tiny && b > tiny) local_max = fmax(local_max, cosang);
+        if (!(cosang > tol)) continue;
+        const double zeta = (b - a) / (2.0 * g);
+        const double t = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t);
+        const double sn = c * t;
+        for (int r = lane; r < nrows; r += 32) {
+          const double u = xi[r], v = xj[r];
+          xi[r] = c * u - sn * v;
+          xj[r] = sn * u + c * v;
+        }
+      }
+      if (!grid_barrier(fl, nblocks)) return;
+      if (step == 0 && blockIdx.x == 0 && threadIdx.x == 0)
+        atomicExch(&fl->off_max[(sweep + 1) & 1], 0ull);
+    }
+    // block maximum of the warps' local maxima, then one atomic per block
+    __shared__ double s_max[kJacobiThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) local_max = fmax(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+    if (lane == 0) s_max[threadIdx.x / 32] = local_max;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = 0.0;
+      for (int w = 0; w < kJacobiThreads / 32; ++w) m = fmax(m, s_max[w]);
+      if (m > 0.0)
+        atomicMax(&fl->off_max[sweep & 1], (unsigned long long)__double_as_longlong(m));
+    }
+    if (!grid_barrier(fl, nblocks)) return;
+    const double m = __longlong_as_double(
+        (long long)(*(volatile unsigned long long*)&fl->off_max[sweep & 1]));
+    if (!(m > tol)) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) fl->sweeps = sweep + 1;
+      return;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    fl->sweeps = max_sweeps;
+    atomicExch(&fl->noconv, 1);
+  }
+}
+
 __global__ void identity_kernel(double* x, int n) {
   const long long nn = (long long)n * n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn;
@@ -228,8 +320,9 @@ int jacobi_onesided(cudaStream_t s, double* X, int nrows, int ncols, double* V, 
   const double tol = 2.220446049250313e-16 * std::sqrt((double)(nrows > 1 ? nrows : 1));
   int nprob = 1;
   long long pstride = 0;
+  double tiny_rel = 1e-32;
   void* args[] = {&X, &nrows, &ncols, (void*)&npad, &V, &flags, &max_sweeps, (void*)&tol,
-                  &nprob, &pstride};
+                  &nprob, &pstride, &tiny_rel};
   if (cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(grid), dim3(kJacobiThreads), args,
                                   0, s) != cudaSuccess)
     return -3;
@@ -249,15 +342,27 @@ int jacobi_batched(cudaStream_t s, double* X, int nrows, int ncols, int nprob, l
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, kJacobiThreads, 0);
   if (per_sm < 1) return -3;
-  long long want = (long long)(npad / 2) * nprob;
+  const bool warp_mode = tol_override > 0.0;  // values only: one warp per pair
+  const long long per_block = warp_mode ? kJacobiThreads / 32 : 1;
+  long long want = ((long long)(npad / 2) * nprob + per_block - 1) / per_block;
   int grid = (int)(want < (long long)nsm ? want : (long long)nsm);  // one block per SM
   if (cudaMemsetAsync(flags, 0, kDevFlagsResetBytes, s) != cudaSuccess) return -3;
   const double tol = tol_override > 0.0
                          ? tol_override
                          : 2.220446049250313e-16 * std::sqrt((double)(nrows > 1 ? nrows : 1));
   double* V = nullptr;
+  double tiny_rel = warp_mode ? 1e-24 : 1e-32;
+  if (warp_mode) {
+    void* wargs[] = {&X, &nrows, &ncols, (void*)&npad, &flags, &max_sweeps, (void*)&tol,
+                     &nprob, &pstride, &tiny_rel};
+    if (cudaLaunchCooperativeKernel((void*)jacobi_warp_kernel, dim3(grid), dim3(kJacobiThreads),
+                                    wargs, 0, s) != cudaSuccess)
+      return -3;
+    ++*launches;
+    return 0;
+  }
   void* args[] = {&X, &nrows, &ncols, (void*)&npad, &V, &flags, &max_sweeps, (void*)&tol,
-                  &nprob, &pstride};
+                  &nprob, &pstride, &tiny_rel};
   if (cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(grid), dim3(kJacobiThreads), args,
                                   0, s) != cudaSuccess)
     return -3;
@@ -401,64 +506,65 @@ cudaError_t normalize_f64(cudaStream_t s, double* x, long long n, double* scratc
 // (shifted CholeskyQR: Fukaya, Kannan, Nakatsukasa, Yamamoto & Yanagisawa,
 // SIAM J. Sci. Comput. 42, A477 (2020)), and a strided copy.
 // ---------------------------------------------------------------------------
-__global__ void chol_diag_kernel(double* __restrict__ G, int lda, int j0, int jb,
-                                 double* __restrict__ Linv, double floor, int* floored,
-                                 double tau, int* __restrict__ defmask) {
-  __shared__ double L[32][33];
-  const int t = threadIdx.x;  // 256 threads
-  for (int e = t; e < 32 * 32; e += blockDim.x) {
-    const int i = e / 32, j = e % 32;
-    L[i][j] = (i < jb && j < jb && j <= i) ? G[(long long)(j0 + i) * lda + j0 + j] : 0.0;
-  }
-  __syncthreads();
-  __shared__ int s_def;
-  for (int k = 0; k < jb; ++k) {
-    if (t == 0) {
-      double dkk = L[k][k];
-      s_def = 0;
-      if (defmask && !(dkk > tau)) {
-        // column k is (numerically) in the span of the earlier ones: decouple it
-        // (unit pivot, no elimination) and mark it for replacement
-        defmask[j0 + k] = 1;
-        s_def = 1;
+// One warp: lane i holds row i of the (<= 32 x 32) diagonal block in registers;
+// right-looking Cholesky with shuffles, then lane j forms column j of the
+// inverse by forward substitution.
+__global__ void __launch_bounds__(32)
+chol_diag_kernel(double* __restrict__ G, int lda, int j0, int jb, double* __restrict__ Linv,
+                 double floor, int* floored, double tau, int* __restrict__ defmask) {
+  const int lane = threadIdx.x;
+  double a[32];
+  double rinv[32];  // 1 / L[k][k], reused by the inverse (one division per pivot)
+#pragma unroll
+  for (int j = 0; j < 32; ++j)
+    a[j] = (lane < jb && j < jb && j <= lane) ? G[(long long)(j0 + lane) * lda + j0 + j] : 0.0;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    if (k < jb) {
+      double dkk = __shfl_sync(0xffffffffu, a[k], k);
+      int def = 0;
+      if (defmask && !(dkk > tau)) {  // column k lies in the span of the earlier ones
+        def = 1;
         dkk = 1.0;
       } else if (!(dkk > floor)) {
         dkk = floor;
-        atomicAdd(floored, 1);
+        if (lane == 0) atomicAdd(floored, 1);
       }
-      L[k][k] = sqrt(dkk);
+      if (def && lane == 0) defmask[j0 + k] = 1;
+      const double piv = sqrt(dkk);
+      const double rp = 1.0 / piv;
+      rinv[k] = rp;
+      if (lane == k) a[k] = piv;
+      if (lane > k) a[k] = def ? 0.0 : a[k] * rp;
+      const double lk = a[k];  // L[lane][k]
+#pragma unroll
+      for (int j = k + 1; j < 32; ++j) {
+        const double ljk = __shfl_sync(0xffffffffu, lk, j);  // L[j][k]
+        if (j < jb && j <= lane) a[j] -= lk * ljk;
+      }
     }
-    __syncthreads();
-    const double piv = L[k][k];
-    for (int i = k + 1 + t; i < jb; i += blockDim.x) L[i][k] = s_def ? 0.0 : L[i][k] / piv;
-    __syncthreads();
-    for (int e = t; e < 32 * 32; e += blockDim.x) {
-      const int i = e / 32, j = e % 32;
-      if (j > k && j <= i && i < jb) L[i][j] -= L[i][k] * L[j][k];
-    }
-    __syncthreads();
   }
-  // write L (lower) back, zero above the diagonal inside the block
-  for (int e = t; e < jb * jb; e += blockDim.x) {
-    const int i = e / jb, j = e % jb;
-    G[(long long)(j0 + i) * lda + j0 + j] = (j <= i) ? L[i][j] : 0.0;
+  if (lane < jb) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < jb) G[(long long)(j0 + lane) * lda + j0 + j] = (j <= lane) ? a[j] : 0.0;
   }
-  // inverse of the lower-triangular block by forward substitution, one column per thread
-  if (t < jb) {
-    const int cidx = t;
-    double x[32];
-    for (int i = 0; i < jb; ++i) {
-      double acc = (i == cidx) ? 1.0 : 0.0;
-      for (int k = cidx; k < i; ++k) acc -= L[i][k] * x[k];
-      x[i] = (i >= cidx) ? acc / L[i][i] : 0.0;
-    }
-    for (int i = 0; i < 32; ++i) Linv[i * 32 + cidx] = (i < jb) ? x[i] : 0.0;
+  // X = L^{-1}: lane j keeps column j; row i needs L[i][k] (k < i) from lane i
+  double x[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) {
+    double acc = (i == lane) ? 1.0 : 0.0;
+#pragma unroll
+    for (int k = 0; k < i; ++k) acc -= __shfl_sync(0xffffffffu, a[k], i) * x[k];
+    x[i] = (i < jb) ? acc * rinv[i] : 0.0;
   }
+#pragma unroll
+  for (int i = 0; i < 32; ++i) Linv[i * 32 + lane] = (i < jb && lane < jb) ? x[i] : 0.0;
 }
 
 cudaError_t chol_diag(cudaStream_t s, double* G, int lda, int j0, int jb, double* Linv,
                       double floor, int* floored, double tau, int* defmask) {
-  chol_diag_kernel<<<1, 256, 0, s>>>(G, lda, j0, jb, Linv, floor, floored, tau, defmask);
+  chol_diag_kernel<<<1, 32, 0, s>>>(G, lda, j0, jb, Linv, floor, floored, tau, defmask);
   return cudaGetLastError();
 }
 
@@ -488,28 +594,32 @@ cudaError_t replace_flagged(cudaStream_t s, double* Q, int rows, int n, int* def
   return cudaGetLastError();
 }
 
-// d[i] = sqrt(G[i][i]) (or 1 if zero); G[i][j] /= d[i] d[j]; G[i][i] += shift_rel * trace-normalised
-__global__ void gram_scale_kernel(double* __restrict__ G, int n, double* __restrict__ d,
-                                  double shift_rel) {
-  __shared__ double s_tr;
-  if (threadIdx.x == 0) s_tr = 0.0;
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+// d[i] = sqrt(G[i][i]) (or 1 if zero), then G[i][j] /= d[i] d[j] and
+// G[i][i] += shift_rel * n (the trace of the scaled Gram is n).
+__global__ void gram_diag_kernel(const double* __restrict__ G, int n, double* __restrict__ d) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const double g = G[(long long)i * n + i];
     d[i] = g > 0.0 ? sqrt(g) : 1.0;
   }
-  __syncthreads();
-  for (long long e = threadIdx.x; e < (long long)n * n; e += blockDim.x) {
-    const long long i = e / n, j = e % n;
-    G[e] /= d[i] * d[j];
+}
+
+__global__ void gram_scale_kernel(double* __restrict__ G, int n, const double* __restrict__ d,
+                                  double shift) {
+  const long long nn = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / n, j = e - i * n;
+    double v = G[e] / (d[i] * d[j]);
+    if (i == j) v += shift;
+    G[e] = v;
   }
-  __syncthreads();
-  // after scaling every nonzero diagonal is 1, so the trace is n: shift = shift_rel * n
-  for (int i = threadIdx.x; i < n; i += blockDim.x) G[(long long)i * n + i] += shift_rel * n;
 }
 
 cudaError_t gram_scale(cudaStream_t s, double* G, int n, double* d, double shift_rel) {
-  gram_scale_kernel<<<1, 1024, 0, s>>>(G, n, d, shift_rel);
+  gram_diag_kernel<<<(n + 255) / 256, 256, 0, s>>>(G, n, d);
+  long long blocks = ((long long)n * n + 255) / 256;
+  if (blocks > 1024) blocks = 1024;
+  gram_scale_kernel<<<(unsigned)blocks, 256, 0, s>>>(G, n, d, shift_rel * n);
   return cudaGetLastError();
 }
 
