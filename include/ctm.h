@@ -49,7 +49,9 @@ enum {
 };
 
 enum { CTM_LEFT = 0, CTM_UP = 1, CTM_RIGHT = 2, CTM_DOWN = 3 };
-enum { CTM_STANDARD = 0, CTM_REDUCED_SEQUENTIAL = 1 };
+/* CTM_REDUCED_ENV: the intermediate method of Sec. III (reduced environment,
+ * 4-index isometry, double-layer absorption, O(chi^3 D^4)). */
+enum { CTM_STANDARD = 0, CTM_REDUCED_SEQUENTIAL = 1, CTM_REDUCED_ENV = 2 };
 /* Arithmetic of the absorption / renormalisation contractions.  Projector
  * factorisations, normalisation, spectra and observables are FP64 always. */
 enum { CTM_FP64 = 0, CTM_TF32 = 1, CTM_BF16 = 2 };

@@ -14,8 +14,9 @@ Methods for PEPS"):
   truncates the grown bonds with projectors P = v v^T, where v holds the leading
   left singular vectors of the upper half of the 2x2 cell ("standard").
 * Sec. III and Fig. 3: the reduced environment, where the right half of that
-  network is replaced by the right-move tensors {C^2, T^3}, and the further
-  one-row approximation {C'^1, T'^2, C'^2}.
+  network is replaced by the right-move tensors {C^2, T^3} ("reduced_env" mode,
+  double-layer absorption), and the further one-row approximation
+  {C'^1, T'^2, C'^2}.
 * Sec. IV and Fig. 4: the split isometries v = v^1 v^2 (v^1 from an SVD of the
   reduced network reshaped chi D x chi D, v^2 from an SVD of the (chi' D, chi)
   matrix) and the sequential ket-then-bra absorption.
@@ -262,6 +263,31 @@ def projector_standard(V, x, sites, chi):
     return v.reshape(na, D, D, v.shape[1])
 
 
+def projector_reduced_env(V, x, sites, chi):
+    """v_{x/y} for the bond below x from the reduced environment (Sec. III, Fig. 3a-b).
+
+    The right half {y, T2_y, C2_y, T3_y} of the standard upper half is replaced
+    by the right-move tensors {C2_x, T3_x}; the isometry v of that right move
+    is dropped, leaving Q = E_L (C2_x T3_x), a (chi D^2) x chi matrix whose
+    leading min(chi, rows) left singular vectors give v (alpha, D, D, chi).
+    """
+    D = sites[x].shape[1]
+    ax = double_layer(sites[x])
+    C1, T1, T2x = V("C", 1, x), V("T", 1, x), V("T", 2, x)
+    C2, T3 = V("C", 2, x), V("T", 3, x)
+    T1f = T1.reshape(T1.shape[0], D * D, T1.shape[3])
+    T2xf = T2x.reshape(T2x.shape[0], D * D, T2x.shape[3])
+    T3f = T3.reshape(T3.shape[0], D * D, T3.shape[3])
+    EL = ein("dg,gUe->dUe", C1, T2xf)
+    EL = ein("dUe,aLd->aLUe", EL, T1f)
+    EL = ein("aLUe,ULXR->aXeR", EL, ax)
+    R = ein("ez,zRb->eRb", C2, T3f)
+    Q = ein("aXeR,eRb->aXb", EL, R)
+    na, nb = Q.shape[0], Q.shape[2]
+    v = trunc_left(Q.reshape(na * D * D, nb), min(chi, na * D * D))
+    return v.reshape(na, D, D, v.shape[1])
+
+
 def split_projector(Mt, chi, chip):
     """Split isometries from a 4-leg network Mt[alpha, k, b, beta] (Sec. IV, Fig. 4a).
 
@@ -327,6 +353,8 @@ def column_absorb(env, r, sites_r, chi, chip, mode):
     for x in "ab":
         if mode == "standard":
             P[x] = projector_standard(V, x, sites_r, chi)
+        elif mode == "reduced_env":
+            P[x] = projector_reduced_env(V, x, sites_r, chi)
         elif mode == "reduced_sequential":
             P[x] = projector_reduced_seq(V, x, sites_r, chi, chip)
         else:
@@ -335,7 +363,7 @@ def column_absorb(env, r, sites_r, chi, chip, mode):
     for x in "ab":
         y = OTHER[x]
         S = edge_site_T1(sites_r[x])
-        if mode == "standard":
+        if mode in ("standard", "reduced_env"):
             vb, vt = P[x], P[y]
             new[("T", 1, y)] = absorb_edge_double(V("T", 1, x), S, vb, vt)
         else:

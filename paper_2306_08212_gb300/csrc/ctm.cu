@@ -68,7 +68,7 @@ struct ctm_ctx {
     double* p = nullptr;
     int rows = 0, k = 0;
   };
-  CacheEntry cache[64];
+  CacheEntry cache[64];  // 0..47 split isometries, 48..55 standard, 56..63 reduced-env
   int* floored = nullptr;  // CholeskyQR pivots floored (device counter)
   // CUDA graphs of steady-state moves (mixed precision, reduced-sequential)
   struct GraphEvent {
@@ -847,6 +847,39 @@ Proj projector_standard(ctm_ctx* c, int r, int x) {
   return P;
 }
 
+// Reduced-environment projector of the bond below x (Sec. III, Fig. 3a-b): the
+// right half of the standard network is replaced by the right-move tensors
+// {C2_x, T3_x} (their isometry drops out), so Q = E_L (C2_x T3_x) is a
+// (chi D^2) x chi matrix.
+Proj projector_reduced_env(ctm_ctx* c, int r, int x) {
+  const int D = c->D;
+  Ten ax = dbl_layer(c, r, x);
+  Ten C1 = E(c, 0, 1, x, r), T1 = edge_fused(E(c, 1, 1, x, r));
+  Ten T2x = edge_fused(E(c, 1, 2, x, r));
+  Ten C2 = E(c, 0, 2, x, r), T3 = edge_fused(E(c, 1, 3, x, r));
+  Tmp EL;
+  {
+    Tmp y1 = ein(c, "dg,gUe->dUe", C1, T2x);
+    Tmp y2 = ein(c, "dUe,aLd->aLUe", y1, T1);
+    y1.release();
+    EL = ein(c, "aLUe,ULXR->aXeR", y2, ax);
+  }
+  Tmp R = ein(c, "ez,zRb->eRb", C2, T3);
+  Tmp Q = ein(c, "aXeR,eRb->aXb", EL, R);
+  EL.release();
+  const int na = Q.t.dims[0], nb = Q.t.dims[2];
+  const int rows = na * D * D, cols = nb;
+  const int k = std::min(c->chi, rows);
+  const bool fast = c->precision != CTM_FP64 && std::min(rows, cols) > kFastMinSide && k < rows &&
+                    k <= cols;
+  Proj P;
+  Tmp U = fast ? left_svd_power(c, Q.t.p, rows, cols, k, 56 + r * 2 + x)
+               : left_svd(c, Q.t.p, rows, cols, k);
+  P.v = std::move(U);
+  P.v.t = view(P.v.t, {na, D, D, k});
+  return P;
+}
+
 // Split isometries from a 4-leg network Mt[alpha, k, b, beta] (Sec. IV, Fig. 4a).
 // Also returns N = v1^T Mt (for reuse by the caller).
 void split_projector(ctm_ctx* c, const Ten& Mt, Tmp& v1, Tmp& v2, Tmp& N, int slot) {
@@ -953,7 +986,9 @@ void column_absorb(ctm_ctx* c, int r, int mode, int col) {
     stream_dep(c, c->side[1], main);
   } else {
     for (int x = 0; x < 2; ++x)
-      P[x] = (mode == CTM_STANDARD) ? projector_standard(c, r, x) : projector_seq(c, r, x, col);
+      P[x] = mode == CTM_STANDARD      ? projector_standard(c, r, x)
+             : mode == CTM_REDUCED_ENV ? projector_reduced_env(c, r, x)
+                                       : projector_seq(c, r, x, col);
   }
   Tmp newT[2], newC1[2], newC4[2];
   for (int x = 0; x < 2; ++x) {
@@ -964,7 +999,7 @@ void column_absorb(ctm_ctx* c, int r, int mode, int col) {
     site(c, r, x, S);
     Tmp Xc = ein(c, "dg,gkbe->dkbe", C1, T2);
     Tmp Xc4 = ein(c, "lu,rkbl->rukb", C4, T4);
-    if (mode == CTM_STANDARD) {
+    if (mode == CTM_STANDARD || mode == CTM_REDUCED_ENV) {  // double-layer absorption
       const Proj& vb = P[x];
       const Proj& vt = P[y];
       const int D2 = c->D * c->D;
@@ -1494,14 +1529,16 @@ int ctm_init_env(ctm_ctx** out, const double* A, const double* B, int d, int D, 
 }
 
 int ctm_move(ctm_ctx* c, int dir, int mode) {
-  if (!c || dir < 0 || dir > 3 || (mode != CTM_STANDARD && mode != CTM_REDUCED_SEQUENTIAL))
+  if (!c || dir < 0 || dir > 3 ||
+      (mode != CTM_STANDARD && mode != CTM_REDUCED_SEQUENTIAL && mode != CTM_REDUCED_ENV))
     return CTM_ERR_ARG;
   return guarded(c, [&] { do_move(c, dir, mode); });
 }
 
 int ctm_converge(ctm_ctx* c, int mode, int max_iter, double tol, int* iters_done,
                  double* last_delta) {
-  if (!c || max_iter < 1 || (mode != CTM_STANDARD && mode != CTM_REDUCED_SEQUENTIAL))
+  if (!c || max_iter < 1 ||
+      (mode != CTM_STANDARD && mode != CTM_REDUCED_SEQUENTIAL && mode != CTM_REDUCED_ENV))
     return CTM_ERR_ARG;
   bool converged = false;
   int rc = guarded(c, [&] {

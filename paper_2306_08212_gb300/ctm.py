@@ -16,11 +16,12 @@ LIB_PATH = os.path.join(HERE, "libctm.so")
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_NAN, ERR_NOCONV, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 LEFT, UP, RIGHT, DOWN = 0, 1, 2, 3
-STANDARD, REDUCED_SEQUENTIAL = 0, 1
+STANDARD, REDUCED_SEQUENTIAL, REDUCED_ENV = 0, 1, 2
 FP64, TF32, BF16 = 0, 1, 2
 INIT_NO_GROW = 0x100
 DIRS = {"left": LEFT, "up": UP, "right": RIGHT, "down": DOWN}
-MODES = {"standard": STANDARD, "reduced_sequential": REDUCED_SEQUENTIAL}
+MODES = {"standard": STANDARD, "reduced_sequential": REDUCED_SEQUENTIAL,
+         "reduced_env": REDUCED_ENV}
 PRECISIONS = {"fp64": FP64, "tf32": TF32, "bf16": BF16}
 
 _lib = None

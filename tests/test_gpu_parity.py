@@ -14,7 +14,7 @@ from paper_2306_08212_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 TOL = 1e-10
-MODES = ["standard", "reduced_sequential"]
+MODES = ["standard", "reduced_env", "reduced_sequential"]
 
 
 @pytest.fixture(scope="module")
@@ -102,7 +102,7 @@ def test_single_move_matches_oracle(ctm, mode, direction):
 # iterations, 5e-10 after 8 and O(1e-2) after 20 (measured with the oracle
 # against itself), so no two FP64 implementations can agree beyond a few
 # iterations.  The standard iteration contracts (differences stay ~1e-15).
-ITERS = {"standard": 20, "reduced_sequential": 4}
+ITERS = {"standard": 20, "reduced_env": 4, "reduced_sequential": 4}
 
 
 @pytest.mark.parametrize("mode", MODES)

@@ -70,7 +70,10 @@ def _env_fold(A, B):
     return {k: O._normalize(v) for k, v in env.items()}
 
 
-@pytest.mark.parametrize("mode", ["standard", "reduced_sequential"])
+MODES = ["standard", "reduced_env", "reduced_sequential"]
+
+
+@pytest.mark.parametrize("mode", MODES)
 def test_fold_and_exact_moves_match_brute_force(mode):
     d, D = 2, 2
     A, B = I.random_sites(d, D, 11)
@@ -91,7 +94,7 @@ def test_fold_and_exact_moves_match_brute_force(mode):
         np.testing.assert_allclose(rho / np.trace(rho), ref / np.trace(ref), atol=1e-12)
 
 
-@pytest.mark.parametrize("mode", ["standard", "reduced_sequential"])
+@pytest.mark.parametrize("mode", MODES)
 def test_exact_vertical_moves_match_brute_force(mode):
     d, D = 2, 2
     A, B = I.random_sites(d, D, 12)
@@ -107,7 +110,7 @@ def test_exact_vertical_moves_match_brute_force(mode):
         np.testing.assert_allclose(rho / np.trace(rho), ref / np.trace(ref), atol=1e-12)
 
 
-@pytest.mark.parametrize("mode", ["standard", "reduced_sequential"])
+@pytest.mark.parametrize("mode", MODES)
 def test_product_state_factorises(mode):
     pa = np.array([0.8, 0.6])
     pb = np.array([0.28, -0.96])
@@ -161,7 +164,7 @@ def _ising_run(beta, chi, mode, plus_boundary, iters):
     return lk, zz, m
 
 
-@pytest.mark.parametrize("mode", ["standard", "reduced_sequential"])
+@pytest.mark.parametrize("mode", MODES)
 def test_ising_high_temperature_matches_onsager(mode):
     beta = 0.40
     lk, zz, m = _ising_run(beta, 16, mode, False, 60)
@@ -170,10 +173,37 @@ def test_ising_high_temperature_matches_onsager(mode):
     assert abs(m) < 1e-10
 
 
-@pytest.mark.parametrize("mode", ["standard", "reduced_sequential"])
+@pytest.mark.parametrize("mode", MODES)
 def test_ising_ordered_phase_matches_onsager_and_yang(mode):
     beta = 0.48
     lk, zz, m = _ising_run(beta, 16, mode, True, 60)
     assert abs(lk - ON.lnz_single_integral(beta)) < 2e-6
     assert abs(zz - ON.nn_correlation(beta)) < 2e-4
     assert abs(m - ON.magnetization(beta)) < 2e-4
+
+
+def test_reduced_env_projector_is_the_standard_one_when_the_right_half_is_exact():
+    """Sec. III: the right half {y, T2_y, C2_y, T3_y} of the standard network is
+    what a right-move absorption turns into {C2_x, T3_x}.  After one exact
+    (untruncated) right column absorption the reduced network is therefore the
+    standard upper half of the previous environment with its columns regrouped,
+    and both give the same projector v v^T."""
+    A, B = I.random_sites(2, 2, 21)
+    env0 = _env_fold(A, B)
+    env1 = {k: v.copy() for k, v in env0.items()}
+    sites2 = {"a": O.rotate_site(A, 2), "b": O.rotate_site(B, 2)}
+    O.column_absorb(env1, 2, sites2, HUGE, HUGE, "standard")  # one right column, exact
+    sites = {"a": A, "b": B}
+    for chi in (4, 9):
+        v_std = O.projector_standard(O.View(env0, 0), "a", sites, chi)
+        v_red = O.projector_reduced_env(O.View(env1, 0), "a", sites, chi)
+        assert v_std.shape == v_red.shape
+        Ps = O.ein("akbx,KLMx->akbKLM", v_std, v_std)
+        Pr = O.ein("akbx,KLMx->akbKLM", v_red, v_red)
+        np.testing.assert_allclose(Pr, Ps, rtol=0, atol=1e-10)
+    # and a planted mistake (x's right half taken from y) breaks it
+    v_bad = O.projector_reduced_env(O.View(env1, 0), "b", {"a": B, "b": A}, 4)
+    Pb = O.ein("akbx,KLMx->akbKLM", v_bad, v_bad)
+    v_std = O.projector_standard(O.View(env0, 0), "a", sites, 4)
+    Ps = O.ein("akbx,KLMx->akbKLM", v_std, v_std)
+    assert np.abs(Pb - Ps).max() > 1e-3
