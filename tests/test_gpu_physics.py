@@ -1,0 +1,104 @@
+"""GPU runs checked against exact results and invariants rather than the oracle.
+
+* Ising-norm PEPS (BASELINE config 2): ln Z per site (Onsager), nearest-neighbour
+  <s s'> and the magnetisation (Yang), every mode, through ctm_converge.
+* Full-size workload of the bench (d=2, D=8, chi=256) in mixed precision: the
+  spectra are descending, non-negative and normalised, energies lie in the
+  spectrum of S.S, and BF16 agrees with TF32 to the BF16 error level.
+* Config 3 (D=6, chi=144): TF32 and BF16 errors against the FP64 path, printed.
+"""
+import numpy as np
+import pytest
+
+from oracle import ctm_oracle as O
+from oracle import onsager as ON
+from paper_2306_08212_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctm():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2306_08212_gb300 import ctm as C
+    C.load()
+    return C
+
+
+SZ = np.diag([1.0, -1.0])
+
+
+@pytest.mark.parametrize("mode", ["standard", "reduced_env", "reduced_sequential"])
+@pytest.mark.parametrize("beta,plus,tol_lnz,tol_nn", [(0.40, False, 2e-6, 2e-4),
+                                                     (0.48, True, 2e-6, 2e-4),
+                                                     (0.44, False, 5e-4, 2e-2)])
+def test_ising_norm_peps_matches_onsager(ctm, mode, beta, plus, tol_lnz, tol_nn):
+    A, W = I.ising_peps(beta)
+    bnd = np.outer(W[0], W[0]) if plus else None
+    g = ctm.Env(A, A, 16, boundary=bnd)
+    try:
+        g.converge(mode, max_iter=40, tol=1e-12)
+        lnz = g.log_kappa()
+        nn = g.expect_bond(0, np.kron(SZ, SZ))
+        m = g.expect_bond(0, np.kron(SZ, np.eye(2)))
+        assert abs(lnz - ON.lnz_single_integral(beta)) < tol_lnz
+        assert abs(nn - ON.nn_correlation(beta)) < tol_nn
+        assert abs(abs(m) - ON.magnetization(beta)) < max(tol_nn, 2e-4 if plus else 1e-8)
+        # the four bonds are equivalent for this uniform state
+        for b in range(1, 4):
+            assert abs(g.expect_bond(b, np.kron(SZ, SZ)) - nn) < tol_nn
+    finally:
+        g.free()
+
+
+def _spectra_ok(spectra):
+    for s in spectra:
+        assert np.all(np.isfinite(s)) and np.all(s >= 0)
+        assert np.all(np.diff(s) <= 1e-15)
+        assert abs(np.sum(s * s) - 1.0) < 1e-12
+
+
+def test_full_size_bench_workload_properties(ctm):
+    A, B = I.random_sites(2, 8, 0)
+    H = O.heisenberg_bond()
+    out = {}
+    for prec in ("tf32", "bf16"):
+        g = ctm.Env(A, B, 256, precision=prec)
+        try:
+            for d in O.MOVE_ORDER:
+                g.move(d, "reduced_sequential")
+            spec = g.corner_spectra()
+            _spectra_ok(spec)
+            assert all(len(s) == 256 for s in spec)
+            en = [g.expect_bond(b, H) for b in range(4)]
+            assert all(-0.75 - 1e-9 <= e <= 0.25 + 1e-9 for e in en)
+            assert np.isfinite(g.log_kappa())
+            out[prec] = (en, spec)
+        finally:
+            g.free()
+    de = max(abs(a - b) for a, b in zip(out["tf32"][0], out["bf16"][0]))
+    ds = max(np.abs(a[:32] - b[:32]).max() for a, b in zip(out["tf32"][1], out["bf16"][1]))
+    print(f"D=8 chi=256: |E_bf16 - E_tf32| = {de:.3e}, top-32 spectra {ds:.3e}")
+    assert de < 1e-2 and ds < 5e-2
+
+
+def test_config3_precision_errors_vs_fp64(ctm):
+    A, B = I.random_sites(2, 6, 0)
+    H = O.heisenberg_bond()
+    res = {}
+    for prec in ("fp64", "tf32", "bf16"):
+        g = ctm.Env(A, B, 144, precision=prec)
+        try:
+            for _ in range(2):
+                for d in O.MOVE_ORDER:
+                    g.move(d, "reduced_sequential")
+            res[prec] = ([g.expect_bond(b, H) for b in range(4)], g.corner_spectra())
+        finally:
+            g.free()
+    for prec, bound in (("tf32", 1e-3), ("bf16", 1e-2)):
+        de = max(abs(a - b) for a, b in zip(res[prec][0], res["fp64"][0]))
+        ds = max(np.abs(a[:32] - b[:32]).max() for a, b in zip(res[prec][1], res["fp64"][1]))
+        print(f"config 3 (D=6, chi=144) {prec}: |dE_bond| = {de:.3e}, top-32 spectra {ds:.3e}")
+        assert de < bound and ds < 10 * bound
