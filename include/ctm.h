@@ -181,6 +181,23 @@ int ctm_singular_values_noalloc(const double* M, int rows, int cols, double* s,
 int ctm_contract_test(int precision, long long M, long long N, long long K, const double* A,
                       const double* B, double* C);
 
+/*
+ * Batching of independent states (no counterpart in the paper: many iPEPS
+ * states, e.g. of different D and chi, advanced together).  A batch refers to
+ * existing contexts (it does not own them; free the batch before them); give
+ * each context its own non-default stream so that their work can overlap.
+ * ctm_batch_move issues the move of direction dir for every state; once every
+ * state is in steady state (bonds at chi, mixed precision, reduced-sequential,
+ * caches warm) the moves of all states are captured into one CUDA graph (forked
+ * from and joined to a stream the batch owns) and later moves replay it as a
+ * single launch.  Results equal those of ctm_move on each context.
+ */
+typedef struct ctm_batch ctm_batch;
+int ctm_batch_create(ctm_batch** out, ctm_ctx** ctxs, int n);
+int ctm_batch_move(ctm_batch* batch, int dir, int mode);
+const char* ctm_batch_last_error(ctm_batch* batch);
+void ctm_batch_free(ctm_batch* batch);
+
 /* Message of the last failure on ctx ("" if none); valid until the next call. */
 const char* ctm_last_error(ctm_ctx* ctx);
 

@@ -33,7 +33,7 @@ void ck(cudaError_t e, const char* what) {
 }
 
 constexpr int kExactSvdMax = 1024;  // exact one-sided Jacobi up to this size
-constexpr int kFastMinSide = 128;   // mixed precision: subspace iteration above this size
+constexpr int kFastMinSide = 0;  // mixed precision: subspace iteration for every size
 constexpr int kOversample = 16;    // randomized range finder: extra columns
 constexpr int kPowerIters = 2;     // randomized range finder: subspace iterations
 constexpr int kMaxSweeps = 60;
@@ -759,7 +759,12 @@ void commit(ctm_ctx* c, int kind, int k, int x, int r, const Ten& src) {
 // (their FP64 Cholesky chains are latency-bound, so overlapping them pays).
 // The host issues the branches one after the other, switching c->stream; in a
 // stream capture the event edges become graph dependencies.
-bool can_fork(ctm_ctx* c) { return c->precision != CTM_FP64 && c->side[0] != nullptr; }
+// Only when every factorisation of the move takes the fast path (no Jacobi,
+// whose device flags a context shares between its launches).
+bool can_fork(ctm_ctx* c) {
+  return c->precision != CTM_FP64 && c->side[0] != nullptr && c->chi * c->D > kFastMinSide &&
+         c->chip * c->D > kFastMinSide;
+}
 
 cudaEvent_t fork_event(ctm_ctx* c) {
   if (c->fork_next == c->fork_events.size()) {
@@ -1083,6 +1088,13 @@ bool graph_eligible(ctm_ctx* c, int mode) {
          mode == CTM_REDUCED_SEQUENTIAL && !trace_on() && !check_on() && all_bonds_at(c, c->chi);
 }
 
+// Eager issue of one move (no host synchronisation).
+void issue_move(ctm_ctx* c, int dir, int mode) {
+  c->fork_next = 0;
+  column_absorb(c, dir, mode, 0);
+  column_absorb(c, dir, mode, 1);
+}
+
 // A steady-state move is a fixed launch sequence: once a direction has run
 // eagerly with warm caches, its two column absorptions are captured into a
 // CUDA graph and replayed (every updated tensor flips its ping-pong buffer
@@ -1224,7 +1236,7 @@ std::vector<double> spectrum(ctm_ctx* c, const Ten& C) {
   {
     ProfScope ps(c, 3, 0.0);
     if (jacobi_batched(c->stream, X.t.p, nrows, ncols, 1, 0, c->flags, kMaxSweeps, &c->launches,
-                       kValuesOnlyTol) != 0)
+                       kValuesOnlyTol, true) != 0)
       fail(CTM_ERR_CUDA, "Jacobi launch failed");
   }
   Tmp sig(c, {ncols});
@@ -1285,7 +1297,7 @@ std::vector<std::vector<double>> spectra_all(ctm_ctx* c) {
   {
     ProfScope ps(c, 3, 0.0);
     if (jacobi_batched(c->stream, X.t.p, nrows, ncols, 8, per, c->flags, kMaxSweeps,
-                       &c->launches, kValuesOnlyTol) != 0)
+                       &c->launches, kValuesOnlyTol, true) != 0)
       fail(CTM_ERR_CUDA, "Jacobi launch failed");
   }
   Tmp sig(c, {8, ncols});
@@ -1465,6 +1477,7 @@ int ctm_init_env(ctm_ctx** out, const double* A, const double* B, int d, int D, 
   int rc = guarded(c, [&] {
     int dev = 0;
     ck(cudaGetDevice(&dev), "device");
+    if (!coop_stream()) fail(CTM_ERR_CUDA, "cooperative stream");
     cudaMemPool_t pool;
     if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
       unsigned long long thr = ~0ull;
@@ -1638,6 +1651,140 @@ int ctm_set_tensor(ctm_ctx* c, int kind, int k, int x, const double* in, const i
 }
 
 long long ctm_kernel_launches(ctm_ctx* c) { return c ? c->launches : 0; }
+
+}  // extern "C"
+
+struct ctm_batch {
+  std::vector<ctm_ctx*> ctx;
+  cudaStream_t master = nullptr;
+  cudaGraphExec_t g[4][3] = {};
+  long long glaunch[4][3] = {};
+  bool warm[4][3] = {};
+  bool ok = true;
+  std::vector<cudaEvent_t> ev;
+  std::string err;
+};
+
+namespace {
+
+cudaEvent_t batch_event(ctm_batch* b, size_t i) {
+  while (b->ev.size() <= i) {
+    cudaEvent_t e;
+    ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "event");
+    b->ev.push_back(e);
+  }
+  return b->ev[i];
+}
+
+bool batch_eligible(ctm_batch* b, int mode) {
+  for (ctm_ctx* c : b->ctx)
+    if (!graph_eligible(c, mode) || c->prof_mask != 0) return false;
+  return b->ok;
+}
+
+// Every state's move of direction dir on its own stream, as one graph forked
+// from and joined to the batch's master stream (or eagerly until warm).
+void batch_move(ctm_batch* b, int dir, int mode) {
+  const int n = (int)b->ctx.size();
+  if (batch_eligible(b, mode)) {
+    if (!b->g[dir][mode] && b->warm[dir][mode]) {
+      cudaGraph_t graph = nullptr;
+      bool ok = cudaStreamBeginCapture(b->master, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      long long nk = 0;
+      if (ok) {
+        try {
+          for (int i = 0; i < n; ++i) {
+            ctm_ctx* c = b->ctx[i];
+            cudaEvent_t e = batch_event(b, 2 * i);
+            ck(cudaEventRecord(e, b->master), "record");
+            ck(cudaStreamWaitEvent(c->stream, e, 0), "wait");
+            const long long l0 = c->launches;
+            issue_move(c, dir, mode);
+            nk += c->launches - l0;
+            c->launches = l0;
+            cudaEvent_t j = batch_event(b, 2 * i + 1);
+            ck(cudaEventRecord(j, c->stream), "record");
+            ck(cudaStreamWaitEvent(b->master, j, 0), "wait");
+          }
+        } catch (const CtmError&) {
+          ok = false;
+        }
+        if (cudaStreamEndCapture(b->master, &graph) != cudaSuccess) ok = false;
+        if (ok && cudaGraphInstantiate(&b->g[dir][mode], graph, 0) != cudaSuccess) {
+          b->g[dir][mode] = nullptr;
+          ok = false;
+        }
+        if (graph) cudaGraphDestroy(graph);
+      }
+      cudaGetLastError();
+      if (!ok) b->ok = false;
+      b->glaunch[dir][mode] = nk;
+    }
+    if (b->g[dir][mode]) {
+      ck(cudaGraphLaunch(b->g[dir][mode], b->master), "graph launch");
+      cudaEvent_t e = batch_event(b, 2 * n);
+      ck(cudaEventRecord(e, b->master), "record");
+      for (ctm_ctx* c : b->ctx) ck(cudaStreamWaitEvent(c->stream, e, 0), "wait");
+      b->ctx[0]->launches += b->glaunch[dir][mode];
+      for (ctm_ctx* c : b->ctx) check_flags(c);
+      return;
+    }
+  }
+  for (ctm_ctx* c : b->ctx) issue_move(c, dir, mode);  // concurrent on the states' streams
+  for (ctm_ctx* c : b->ctx) check_flags(c);
+  if (batch_eligible(b, mode)) b->warm[dir][mode] = true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ctm_batch_create(ctm_batch** out, ctm_ctx** ctxs, int n) {
+  if (!out || !ctxs || n < 1) return CTM_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!ctxs[i]) return CTM_ERR_ARG;
+  ctm_batch* b = new (std::nothrow) ctm_batch;
+  if (!b) return CTM_ERR_OOM;
+  b->ctx.assign(ctxs, ctxs + n);
+  if (cudaStreamCreateWithFlags(&b->master, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return CTM_ERR_CUDA;
+  }
+  *out = b;
+  return CTM_OK;
+}
+
+int ctm_batch_move(ctm_batch* b, int dir, int mode) {
+  if (!b || dir < 0 || dir > 3 ||
+      (mode != CTM_STANDARD && mode != CTM_REDUCED_SEQUENTIAL && mode != CTM_REDUCED_ENV))
+    return CTM_ERR_ARG;
+  try {
+    batch_move(b, dir, mode);
+    b->err.clear();
+    return CTM_OK;
+  } catch (const CtmError& e) {
+    b->err = e.msg;
+    return e.code;
+  } catch (const std::exception& e) {
+    b->err = e.what();
+    return CTM_ERR_OOM;
+  }
+}
+
+const char* ctm_batch_last_error(ctm_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+void ctm_batch_free(ctm_batch* b) {
+  if (!b) return;
+  if (b->master) cudaStreamSynchronize(b->master);
+  for (auto& row : b->g)
+    for (auto& g : row)
+      if (g) cudaGraphExecDestroy(g);
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  if (b->master) cudaStreamDestroy(b->master);
+  cudaGetLastError();
+  delete b;
+}
 
 int ctm_contract_test(int precision, long long M, long long N, long long K, const double* A,
                       const double* B, double* C) {

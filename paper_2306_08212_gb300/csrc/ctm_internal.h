@@ -94,8 +94,14 @@ int jacobi_onesided(cudaStream_t s, double* X, int nrows, int ncols, double* V,
 // tol_override > 0 replaces the cosine tolerance sqrt(nrows) * eps; singular
 // values alone converge quadratically in the cosines, so 1e-10 already gives
 // them to FP64 accuracy.
+// serialize: issue on the process-wide cooperative stream (see coop_stream).
 int jacobi_batched(cudaStream_t s, double* X, int nrows, int ncols, int nprob, long long pstride,
-                   DevFlags* flags, int max_sweeps, long long* launches, double tol_override);
+                   DevFlags* flags, int max_sweeps, long long* launches, double tol_override,
+                   bool serialize);
+
+// The stream on which every cooperative launch of this library runs (one per
+// device, created on first use).
+cudaStream_t coop_stream();
 constexpr double kValuesOnlyTol = 1e-10;
 
 // Column norms of X (nrows x ncols col-major) into sig[ncols]; perm[r] = index of

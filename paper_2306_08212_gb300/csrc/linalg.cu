@@ -12,6 +12,7 @@
 
 #include <cmath>
 #include <cstddef>
+#include <mutex>
 
 namespace ctm {
 
@@ -292,11 +293,52 @@ cudaError_t fill_identity(cudaStream_t s, double* x, int n) {
 }
 
 int jacobi_batched(cudaStream_t s, double* X, int nrows, int ncols, int nprob, long long pstride,
-                   DevFlags* flags, int max_sweeps, long long* launches, double tol_override);
+                   DevFlags* flags, int max_sweeps, long long* launches, double tol_override,
+                   bool serialize);
+
+// Cooperative launches rely on all their blocks being resident at once; two of
+// them running together (different contexts or streams) could each hold SMs
+// the other waits for.  They are therefore all issued on one stream per device,
+// ordered after and before the caller's stream with events.
+static std::mutex g_coop_mu;
+static cudaStream_t g_coop[64] = {};
+
+cudaStream_t coop_stream() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lock(g_coop_mu);
+  if (!g_coop[dev] && cudaStreamCreateWithFlags(&g_coop[dev], cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    g_coop[dev] = nullptr;
+  }
+  return g_coop[dev];
+}
+
+// Launch fn on the cooperative stream, ordered after the work so far on s and
+// before the work issued later on s.
+static cudaError_t launch_coop_ordered(const void* fn, dim3 grid, dim3 block, void** args,
+                                       cudaStream_t s, bool serialize) {
+  cudaStream_t cs = serialize ? coop_stream() : nullptr;
+  if (!cs) return cudaLaunchCooperativeKernel(fn, grid, block, args, 0, s);
+  cudaEvent_t e1, e2;
+  if (cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) return cudaErrorUnknown;
+  if (cudaEventCreateWithFlags(&e2, cudaEventDisableTiming) != cudaSuccess) {
+    cudaEventDestroy(e1);
+    return cudaErrorUnknown;
+  }
+  cudaError_t e = cudaEventRecord(e1, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, e1, 0);
+  if (e == cudaSuccess) e = cudaLaunchCooperativeKernel(fn, grid, block, args, 0, cs);
+  if (e == cudaSuccess) e = cudaEventRecord(e2, cs);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, e2, 0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  return e;
+}
 
 int jacobi_onesided(cudaStream_t s, double* X, int nrows, int ncols, double* V, DevFlags* flags,
                     int max_sweeps, long long* launches) {
-  if (!V) return jacobi_batched(s, X, nrows, ncols, 1, 0, flags, max_sweeps, launches, 0.0);
+  if (!V) return jacobi_batched(s, X, nrows, ncols, 1, 0, flags, max_sweeps, launches, 0.0, true);
   if (ncols < 2) {
     if (V && ncols == 1) {
       if (fill_identity(s, V, 1) != cudaSuccess) return -3;
@@ -323,8 +365,8 @@ int jacobi_onesided(cudaStream_t s, double* X, int nrows, int ncols, double* V, 
   double tiny_rel = 1e-32;
   void* args[] = {&X, &nrows, &ncols, (void*)&npad, &V, &flags, &max_sweeps, (void*)&tol,
                   &nprob, &pstride, &tiny_rel};
-  if (cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(grid), dim3(kJacobiThreads), args,
-                                  0, s) != cudaSuccess)
+  if (launch_coop_ordered((void*)jacobi_kernel, dim3(grid), dim3(kJacobiThreads), args, s, true) !=
+      cudaSuccess)
     return -3;
   ++*launches;
   return 0;
@@ -334,7 +376,8 @@ int jacobi_onesided(cudaStream_t s, double* X, int nrows, int ncols, double* V, 
 // accumulation) in one cooperative launch: one grid barrier per round-robin
 // step serves all of them.
 int jacobi_batched(cudaStream_t s, double* X, int nrows, int ncols, int nprob, long long pstride,
-                   DevFlags* flags, int max_sweeps, long long* launches, double tol_override) {
+                   DevFlags* flags, int max_sweeps, long long* launches, double tol_override,
+                   bool serialize) {
   if (ncols < 2 || nprob < 1) return 0;
   const int npad = ncols + (ncols & 1);
   int dev = 0, nsm = 0, per_sm = 0;
@@ -355,16 +398,16 @@ int jacobi_batched(cudaStream_t s, double* X, int nrows, int ncols, int nprob, l
   if (warp_mode) {
     void* wargs[] = {&X, &nrows, &ncols, (void*)&npad, &flags, &max_sweeps, (void*)&tol,
                      &nprob, &pstride, &tiny_rel};
-    if (cudaLaunchCooperativeKernel((void*)jacobi_warp_kernel, dim3(grid), dim3(kJacobiThreads),
-                                    wargs, 0, s) != cudaSuccess)
+    if (launch_coop_ordered((void*)jacobi_warp_kernel, dim3(grid), dim3(kJacobiThreads), wargs, s,
+                            serialize) != cudaSuccess)
       return -3;
     ++*launches;
     return 0;
   }
   void* args[] = {&X, &nrows, &ncols, (void*)&npad, &V, &flags, &max_sweeps, (void*)&tol,
                   &nprob, &pstride, &tiny_rel};
-  if (cudaLaunchCooperativeKernel((void*)jacobi_kernel, dim3(grid), dim3(kJacobiThreads), args,
-                                  0, s) != cudaSuccess)
+  if (launch_coop_ordered((void*)jacobi_kernel, dim3(grid), dim3(kJacobiThreads), args, s,
+                          serialize) != cudaSuccess)
     return -3;
   ++*launches;
   return 0;

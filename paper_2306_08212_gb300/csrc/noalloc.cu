@@ -119,7 +119,7 @@ extern "C" int ctm_singular_values_noalloc(const double* M, int rows, int cols, 
       return CTM_ERR_CUDA;
   }
   long long launches = 0;
-  if (jacobi_batched(st, X, nrows, ncols, 1, 0, flags, 60, &launches, kValuesOnlyTol) != 0)
+  if (jacobi_batched(st, X, nrows, ncols, 1, 0, flags, 60, &launches, kValuesOnlyTol, false) != 0)
     return CTM_ERR_CUDA;
   if (column_norms_sorted(st, X, nrows, ncols, sig, perm) != cudaSuccess) return CTM_ERR_CUDA;
   sorted_unit_values_kernel<<<1, 256, 0, st>>>(sig, perm, ncols, s);

@@ -286,18 +286,34 @@ __device__ __forceinline__ float round_tf32(float x) {
   return __uint_as_float(y);
 }
 
+// Tiled: a block packs 32 rows x 256 K-positions; the leg-map offsets of its
+// rows and K-positions are computed once into shared memory, and writes run
+// along K (coalesced).
+constexpr int kPackRows = 32, kPackK = 256;
+
 template <bool TF32>
-__global__ void pack_kernel(void* __restrict__ out, const double* __restrict__ in, LegMap Rm,
-                            LegMap Rk, long long R, long long K, long long Kp) {
-  const long long total = R * Kp;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long r = i / Kp, k = i - r * Kp;
-    const double v = (k < K) ? in[tc_map_offset(Rm, r) + tc_map_offset(Rk, k)] : 0.0;
+__global__ void __launch_bounds__(256)
+pack_kernel(void* __restrict__ out, const double* __restrict__ in, LegMap Rm, LegMap Rk,
+            long long R, long long K, long long Kp) {
+  __shared__ long long offr[kPackRows];
+  __shared__ long long offk[kPackK];
+  const long long r0 = (long long)blockIdx.y * kPackRows;
+  const long long k0 = (long long)blockIdx.x * kPackK;
+  for (int i = threadIdx.x; i < kPackRows; i += blockDim.x)
+    offr[i] = (r0 + i < R) ? tc_map_offset(Rm, r0 + i) : 0;
+  for (int i = threadIdx.x; i < kPackK; i += blockDim.x)
+    offk[i] = (k0 + i < K) ? tc_map_offset(Rk, k0 + i) : 0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < kPackRows * kPackK; e += blockDim.x) {
+    const int i = e / kPackK, j = e % kPackK;
+    const long long r = r0 + i, k = k0 + j;
+    if (r >= R || k >= Kp) continue;
+    const double v = (k < K) ? in[offr[i] + offk[j]] : 0.0;
+    const long long o = r * Kp + k;
     if constexpr (TF32)
-      static_cast<float*>(out)[i] = round_tf32((float)v);
+      static_cast<float*>(out)[o] = round_tf32((float)v);
     else
-      static_cast<__nv_bfloat16*>(out)[i] = __double2bfloat16(v);
+      static_cast<__nv_bfloat16*>(out)[o] = __double2bfloat16(v);
   }
 }
 
@@ -389,10 +405,9 @@ cudaError_t launch(cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb,
 template <bool TF32>
 cudaError_t pack(cudaStream_t s, void* out, const double* in, const LegMap& Rm, const LegMap& Rk,
                  long long R, long long K, long long Kp) {
-  long long blocks = (R * Kp + 255) / 256;
-  if (blocks > 152 * 32) blocks = 152 * 32;
-  if (blocks < 1) blocks = 1;
-  pack_kernel<TF32><<<(unsigned)blocks, 256, 0, s>>>(out, in, Rm, Rk, R, K, Kp);
+  const long long gy = (R + kPackRows - 1) / kPackRows, gx = (Kp + kPackK - 1) / kPackK;
+  if (gy > 65535 || gx > (1ll << 31) - 1) return cudaErrorInvalidConfiguration;
+  pack_kernel<TF32><<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(out, in, Rm, Rk, R, K, Kp);
   return cudaGetLastError();
 }
 

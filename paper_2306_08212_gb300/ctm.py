@@ -47,6 +47,10 @@ SIGNATURES = {
     "ctm_singular_values_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
     "ctm_contract_test": (ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
                                           ctypes.c_longlong, _D, _D, _D]),
+    "ctm_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int]),
+    "ctm_batch_move": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
+    "ctm_batch_last_error": (ctypes.c_char_p, [_P]),
+    "ctm_batch_free": (None, [_P]),
     "ctm_last_error": (ctypes.c_char_p, [_P]),
     "ctm_free": (None, [_P]),
 }
@@ -309,6 +313,39 @@ class Env:
         if self.ctx:
             ctm_free(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent states advanced together (one CUDA graph per direction once warm).
+
+    Create each Env on its own torch.cuda.Stream for the work to overlap.
+    """
+
+    def __init__(self, envs):
+        self.envs = list(envs)
+        arr = (_P * len(self.envs))(*[e.ctx for e in self.envs])
+        self.handle = ctypes.c_void_p()
+        rc = load().ctm_batch_create(ctypes.byref(self.handle), arr, len(self.envs))
+        if rc != OK:
+            raise CtmError(rc, "batch create failed")
+
+    def move(self, direction, mode="reduced_sequential"):
+        d = DIRS[direction] if isinstance(direction, str) else int(direction)
+        m = MODES[mode] if isinstance(mode, str) else int(mode)
+        rc = load().ctm_batch_move(self.handle, d, m)
+        if rc != OK:
+            raise CtmError(rc, load().ctm_batch_last_error(self.handle).decode())
+
+    def free(self):
+        if self.handle:
+            load().ctm_batch_free(self.handle)
+            self.handle = None
 
     def __del__(self):
         try:
