@@ -196,17 +196,26 @@ def _run_native(args):
 
     for _ in range(args.warmup):
         step()
-    # one untimed step with every class timed: the per-class breakdown, and the
-    # class with the most device time among the contractions
+    # untimed profiling steps with every kernel class timed (CUDA events, also
+    # as event nodes of the recaptured graphs): the per-class breakdown of one
+    # steady-state step, and the class with the most device time among the
+    # contractions
     ctm.ctm_kernel_stats_reset(ctx, 0xF)
+    step()
+    step()
+    ctm.ctm_kernel_stats_reset(ctx, 0xF)  # same mask: counters cleared, graphs kept
     step()
     breakdown = ctm.ctm_kernel_stats(ctx)
     gemm_like = [k for k in breakdown if k["flops"] > 0]
     top = max(gemm_like, key=lambda k: k["ms"]) if gemm_like else None
     top_cls = {v: k for k, v in ctm.PROFILE_CLASSES.items()}[top["name"]] if top else None
-    torch.cuda.synchronize()
     # timed region: events only around the launches of that class
-    ctm.ctm_kernel_stats_reset(ctx, (1 << top_cls) if top_cls is not None else 0)
+    top_mask = (1 << top_cls) if top_cls is not None else 0
+    ctm.ctm_kernel_stats_reset(ctx, top_mask)
+    step()
+    step()
+    torch.cuda.synchronize()
+    ctm.ctm_kernel_stats_reset(ctx, top_mask)
     launches0 = ctm.ctm_kernel_launches(ctx)
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
     barrier(dist)

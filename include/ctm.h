@@ -146,10 +146,14 @@ long long ctm_kernel_launches(ctm_ctx* ctx);
  * around every launch of a class (0 = FP64 contraction, 1 = TF32 tensor-core
  * contraction, 2 = BF16 tensor-core contraction, 3 = Jacobi SVD sweep kernel).
  * ctm_profile_enable(ctx, mask) clears the counters and records the classes
- * whose bit (1 << class) is set in mask; 0 stops.
+ * whose bit (1 << class) is set in mask; 0 stops.  Changing the mask discards
+ * the context's recorded CUDA graphs (they are recaptured with event nodes for
+ * the timed classes at the next steady-state moves).
  * ctm_profile_read synchronises the stream and returns, for one class, the
- * launches, their summed device time in ms and their algorithmic flop count
- * (2 M N K for a contraction, 0 for Jacobi whose work depends on the data).
+ * timed launches, their summed device time in ms and their algorithmic flop
+ * count (2 M N K for a contraction, 0 for Jacobi whose work depends on the
+ * data).  When the FP64 class is the only one timed (mask 1), one of its
+ * launches in eight is timed.
  */
 int ctm_profile_enable(ctm_ctx* ctx, int on);
 int ctm_profile_read(ctm_ctx* ctx, int cls, long long* launches, double* ms, double* flops);

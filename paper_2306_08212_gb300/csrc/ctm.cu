@@ -64,6 +64,7 @@ struct ctm_ctx {
   };
   int prof_mask = 0;  // bit cls set: time that class
   ProfClass prof[4];
+  long long prof_seen[4] = {0, 0, 0, 0};  // launches of each class (for sampling)
   struct CacheEntry {  // warm start of the mixed-precision subspace iteration
     double* p = nullptr;
     int rows = 0, k = 0;
@@ -177,13 +178,20 @@ struct ProfScope {
   bool on;
   bool deferred;  // the callee records the two events around the kernel itself
   cudaEvent_t g0 = nullptr, g1 = nullptr;  // event pair owned by a graph being captured
+  // When only the FP64 contractions are timed, one launch in kSampleF64 carries
+  // events, to keep the overhead inside a timed region small.
+  static constexpr int kSampleF64 = 8;
   ProfScope(ctm_ctx* ctx, int k, double flops, bool defer = false)
       : c(ctx), cls(k), on(((ctx->prof_mask >> k) & 1) != 0), deferred(defer) {
+    // sampling only when the FP64 class is timed alone (the timed region), not
+    // in the all-class breakdown
+    if (on && cls == 0 && c->prof_mask == 1 && (c->prof_seen[0]++ % kSampleF64) != 0) on = false;
     if (c->capturing) {
-      // tensor-core launches of a captured move carry their own event pair,
-      // recorded by every replay of the graph
+      // launches of a timed class inside a captured move carry their own event
+      // pair, recorded by every replay of the graph
+      const bool sampled = on;
       on = false;
-      if (cls == 1 || cls == 2) {
+      if (sampled) {
         if (cudaEventCreate(&g0) != cudaSuccess || cudaEventCreate(&g1) != cudaSuccess)
           fail(CTM_ERR_CUDA, "event create");
         c->gev[c->capture_dir].push_back({cls, g0, g1, flops});
@@ -1860,6 +1868,7 @@ int ctm_profile_enable(ctm_ctx* c, int on) {
       pc.count = 0;
       pc.ms = pc.flops = 0.0;
     }
+    if ((on & 0xF) != c->prof_mask) drop_graphs(c);  // re-capture with the new event set
     c->prof_mask = on & 0xF;
   });
 }
