@@ -140,6 +140,15 @@ cudaError_t gemm_f64(cudaStream_t s, long long M, long long N, long long K, doub
     return cudaGetLastError();
   }
   const long long tiles32 = ((M + 31) / 32) * ((N + 31) / 32);
+  if (tiles32 < 152 && K < 512) {
+    // few output tiles and a short K: 16 x 16 tiles put more blocks on the SMs
+    dim3 grid((unsigned)((N + 15) / 16), (unsigned)((M + 15) / 16));
+    if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+    gemm_f64_kernel<16, 16, 16, 1, 1><<<grid, 256, 0, s>>>(M, N, K, alpha, A, Am, Ak, B, Bk, Bn,
+                                                           beta, C, Cm, Cn, a_m_fast, b_n_fast, K,
+                                                           nullptr);
+    return cudaGetLastError();
+  }
   // few output tiles and a long K: split K over more blocks, reduce deterministically
   long long splits = 1;
   if (tiles32 < 2 * 152 && K >= 512) {
