@@ -118,6 +118,15 @@ int ctm_corner_spectrum(ctm_ctx* ctx, int corner, double* s, int* len);
 int ctm_corner_spectra(ctm_ctx* ctx, double* s, int maxlen, int* lens);
 
 /*
+ * Connected correlation along a row (Sec. V, Fig. 9b: S_zz(x)):
+ * out[x-1] = <op1_0 op2_x> - <op1_0><op2_x> for x = 1..xmax, sites 0..x of a
+ * row starting on sublattice a, from the strip closed by C1_a, T1_a, C4_a on
+ * the left and by C2, T3, C3 of site x on the right.  op1, op2: host, d x d
+ * row-major; out: host, xmax doubles.  FP64.
+ */
+int ctm_correlator(ctm_ctx* ctx, const double* op1, const double* op2, int xmax, double* out);
+
+/*
  * Per-site log norm ln kappa = (1/4) ln[Z22 Z00 / (Z20 Z02)] from the 2x2
  * window with top-left site a, where Zhw closes the environment around an
  * h x w block of sites (corner and edge normalisations cancel).  For the

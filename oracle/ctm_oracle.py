@@ -571,3 +571,52 @@ def log_kappa_sites(env, A, B, x="a"):
     if not ratio > 0:
         raise FloatingPointError("non-positive norm ratio")
     return 0.25 * float(np.log(ratio))
+
+
+# ----------------------------------------------------------------------------
+# Row transfer: correlation function along a row (Sec. V, Fig. 9b)
+# ----------------------------------------------------------------------------
+
+def _strip_absorb(V, T2, S, op, T4):
+    """Absorb one column (T2 above, site S with `op` between ket and bra
+    physical legs, T4 below) into the strip vector V[top, k, b, bottom]."""
+    W = ein("tkbr,tKBu->kbrKBu", V, T2)
+    W = ein("kbrKBu,pKkDq->brBupDq", W, S)          # ket: (p, up, left, down, right)
+    W = ein("brBupDq,Pp->brBuPDq", W, op)            # <psi| op |psi>: op[bra, ket]
+    W = ein("brBuPDq,PBbEQ->ruDqEQ", W, S.conj())    # bra
+    return ein("ruDqEQ,vDEr->uqQv", W, T4)
+
+
+def _strip_close(V, C2, T3, C3):
+    X = ein("uqQv,ue->eqQv", V, C2)
+    X = ein("eqQv,eqQg->gv", X, T3)
+    return float(ein("gv,gv->", X, C3))
+
+
+def row_correlator(env, A, B, op1, op2, xmax):
+    """S(x) = <op1_0 op2_x> - <op1_0><op2_x> for sites 0..x of a row starting on
+    sublattice a, x = 1..xmax, from the strip closed by C1_a T1_a C4_a on the left
+    and by C2, T3, C3 of the last site on the right (Sec. V: S_zz(x))."""
+    site = {"a": A, "b": B}
+    d = A.shape[0]
+    ident = np.eye(d)
+    V0 = ein("dt,akbd->tkba", env[("C", 1, "a")], env[("T", 1, "a")])
+    V0 = ein("tkba,ra->tkbr", V0, env[("C", 4, "a")])
+    T2, T4 = env[("T", 2, "a")], env[("T", 4, "a")]
+    Vid = _strip_absorb(V0, T2, A, ident, T4)
+    Vop = _strip_absorb(V0, T2, A, op1, T4)
+    out = []
+    for x in range(1, xmax + 1):
+        s = "a" if x % 2 == 0 else "b"
+        T2, T4, S = env[("T", 2, s)], env[("T", 4, s)], site[s]
+        C2, T3, C3 = env[("C", 2, s)], env[("T", 3, s)], env[("C", 3, s)]
+        nid = _strip_absorb(Vid, T2, S, ident, T4)
+        nop = _strip_absorb(Vop, T2, S, ident, T4)
+        z = _strip_close(nid, C2, T3, C3)
+        one0 = _strip_close(nop, C2, T3, C3) / z
+        onex = _strip_close(_strip_absorb(Vid, T2, S, op2, T4), C2, T3, C3) / z
+        two = _strip_close(_strip_absorb(Vop, T2, S, op2, T4), C2, T3, C3) / z
+        out.append(two - one0 * onex)
+        scale = np.linalg.norm(nid)
+        Vid, Vop = nid / scale, nop / scale
+    return np.array(out)

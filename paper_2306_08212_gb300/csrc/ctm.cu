@@ -1386,6 +1386,68 @@ double expect_bond(ctm_ctx* c, int bond, const double* op_host) {
   return n / dd;
 }
 
+// Row transfer (Sec. V, Fig. 9b): strip vector V[top, k, b, bottom] absorbing
+// one column (T2 above, the site with `op` between its ket and bra physical
+// legs, T4 below).
+Tmp strip_absorb(ctm_ctx* c, const Ten& V, int s, const Ten& op) {
+  Ten S;
+  site(c, 0, s, S);
+  Tmp W = ein64(c, "tkbr,tKBu->kbrKBu", V, E(c, 1, 2, s, 0));
+  W = ein64(c, "kbrKBu,pKkDq->brBupDq", W, S);
+  W = ein64(c, "brBupDq,Pp->brBuPDq", W, op);
+  W = ein64(c, "brBuPDq,PBbEQ->ruDqEQ", W, S);
+  return ein64(c, "ruDqEQ,vDEr->uqQv", W, E(c, 1, 4, s, 0));
+}
+
+double strip_close(ctm_ctx* c, const Ten& V, int s) {
+  Tmp X = ein64(c, "uqQv,ue->eqQv", V, E(c, 0, 2, s, 0));
+  Tmp Y = ein64(c, "eqQv,eqQg->gv", X, E(c, 1, 3, s, 0));
+  Tmp z = ein64(c, "gv,gv->", Y, E(c, 0, 3, s, 0));
+  return scalar_of(c, z.t);
+}
+
+Tmp scaled(ctm_ctx* c, const Ten& V, double f) {
+  Tmp sc(c, {1});
+  sc.t.nd = 0;
+  ck(cudaMemcpyAsync(sc.t.p, &f, sizeof(double), cudaMemcpyHostToDevice, c->stream), "h2d");
+  ck(cudaStreamSynchronize(c->stream), "sync");  // f lives on the host stack
+  return ein64(c, "tkbr,->tkbr", V, sc.t);
+}
+
+void row_correlator(ctm_ctx* c, const double* op1_h, const double* op2_h, int xmax, double* out) {
+  const int d = c->d;
+  Tmp op1(c, {d, d}), op2(c, {d, d}), I = identity(c, d);
+  ck(cudaMemcpyAsync(op1.t.p, op1_h, sizeof(double) * d * d, cudaMemcpyHostToDevice, c->stream),
+     "h2d");
+  ck(cudaMemcpyAsync(op2.t.p, op2_h, sizeof(double) * d * d, cudaMemcpyHostToDevice, c->stream),
+     "h2d");
+  Tmp V0 = ein64(c, "dt,akbd->tkba", E(c, 0, 1, 0, 0), E(c, 1, 1, 0, 0));
+  V0 = ein64(c, "tkba,ra->tkbr", V0, E(c, 0, 4, 0, 0));
+  Tmp Vid = strip_absorb(c, V0, 0, I.t);
+  Tmp Vop = strip_absorb(c, V0, 0, op1.t);
+  for (int x = 1; x <= xmax; ++x) {
+    const int s = x % 2;  // sublattice of site x (site 0 is a)
+    Tmp nid = strip_absorb(c, Vid, s, I.t);
+    Tmp nop = strip_absorb(c, Vop, s, I.t);
+    const double z = strip_close(c, nid, s);
+    const double one0 = strip_close(c, nop, s) / z;
+    double onex, two;
+    {
+      Tmp t1 = strip_absorb(c, Vid, s, op2.t);
+      onex = strip_close(c, t1, s) / z;
+      Tmp t2 = strip_absorb(c, Vop, s, op2.t);
+      two = strip_close(c, t2, s) / z;
+    }
+    if (!std::isfinite(two) || !std::isfinite(one0) || !std::isfinite(onex))
+      fail(CTM_ERR_NAN, "non-finite correlator");
+    out[x - 1] = two - one0 * onex;
+    Tmp nn = ein64(c, "tkbr,tkbr->", nid, nid);
+    const double f = 1.0 / std::sqrt(scalar_of(c, nn.t));
+    Vid = scaled(c, nid, f);
+    Vop = scaled(c, nop, f);
+  }
+}
+
 double log_kappa(ctm_ctx* c) {
   const int x = 0, y = 1, r = 0;
   auto C = [&](int k, int s) { return E(c, 0, k, s, r); };
@@ -1620,6 +1682,11 @@ int ctm_corner_spectra(ctm_ctx* c, double* s, int maxlen, int* lens) {
       lens[i] = n;
     }
   });
+}
+
+int ctm_correlator(ctm_ctx* c, const double* op1, const double* op2, int xmax, double* out) {
+  if (!c || !op1 || !op2 || !out || xmax < 1) return CTM_ERR_ARG;
+  return guarded(c, [&] { row_correlator(c, op1, op2, xmax, out); });
 }
 
 int ctm_log_kappa(ctm_ctx* c, double* value) {

@@ -38,6 +38,7 @@ SIGNATURES = {
     "ctm_expect_bond": (ctypes.c_int, [_P, ctypes.c_int, _D, _D]),
     "ctm_corner_spectrum": (ctypes.c_int, [_P, ctypes.c_int, _D, _I]),
     "ctm_corner_spectra": (ctypes.c_int, [_P, _D, ctypes.c_int, _I]),
+    "ctm_correlator": (ctypes.c_int, [_P, _D, _D, ctypes.c_int, _D]),
     "ctm_log_kappa": (ctypes.c_int, [_P, _D]),
     "ctm_get_tensor": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _I]),
     "ctm_set_tensor": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _I]),
@@ -153,6 +154,14 @@ def ctm_corner_spectra(ctx, maxlen):
     lens = (ctypes.c_int * 8)()
     rc = load().ctm_corner_spectra(ctx, _dptr(s), int(maxlen), lens)
     return rc, [s[i, : lens[i]] for i in range(8)]
+
+
+def ctm_correlator(ctx, op1, op2, xmax):
+    op1 = np.ascontiguousarray(op1, dtype=np.float64)
+    op2 = np.ascontiguousarray(op2, dtype=np.float64)
+    out = np.zeros(int(xmax))
+    rc = load().ctm_correlator(ctx, _dptr(op1), _dptr(op2), int(xmax), _dptr(out))
+    return rc, out
 
 
 def ctm_log_kappa(ctx):
@@ -289,6 +298,11 @@ class Env:
 
     def corner_spectra(self):
         rc, out = ctm_corner_spectra(self.ctx, max(self.chi, 1) * 4 + 16)
+        self._check(rc)
+        return out
+
+    def correlator(self, op1, op2, xmax):
+        rc, out = ctm_correlator(self.ctx, op1, op2, xmax)
         self._check(rc)
         return out
 

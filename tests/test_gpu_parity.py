@@ -197,3 +197,20 @@ def test_error_codes(ctm):
         assert rc == ctm.ERR_ARG
     finally:
         g.free()
+
+
+def test_row_correlator_matches_oracle(ctm):
+    A, B = I.random_sites(2, 3, 8)
+    env = O.init_env(A, B, 18)
+    g = ctm.Env(A, B, 18)
+    try:
+        for d in O.MOVE_ORDER:
+            O.move(env, d, A, B, 18, 18, "standard")
+            g.move(d, "standard")
+        sz = np.diag([0.5, -0.5])
+        sx = np.array([[0, 0.5], [0.5, 0]])
+        ref = O.row_correlator(env, A, B, sz, sx, 6)
+        got = g.correlator(sz, sx, 6)
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-12)
+    finally:
+        g.free()

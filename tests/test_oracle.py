@@ -207,3 +207,36 @@ def test_reduced_env_projector_is_the_standard_one_when_the_right_half_is_exact(
     v_std = O.projector_standard(O.View(env0, 0), "a", sites, 4)
     Ps = O.ein("akbx,KLMx->akbKLM", v_std, v_std)
     assert np.abs(Pb - Ps).max() > 1e-3
+
+
+def test_row_correlator_x1_is_the_bond_expectation():
+    """The strip of two sites is the 1x2 window of the bond density matrix."""
+    A, B = I.random_sites(2, 2, 31)
+    env = O.init_env(A, B, 8)
+    O.converge(env, A, B, 8, 8, "standard", max_iter=5)
+    sz = np.diag([0.5, -0.5])
+    sx = np.array([[0, 0.5], [0.5, 0]])
+    S = O.row_correlator(env, A, B, sz, sx, 3)
+    two = O.expect_bond(env, A, B, 0, np.kron(sz, sx))
+    one_a = O.expect_bond(env, A, B, 0, np.kron(sz, np.eye(2)))
+    one_b = O.expect_bond(env, A, B, 0, np.kron(np.eye(2), sx))
+    assert abs(S[0] - (two - one_a * one_b)) < 1e-13
+
+
+def test_row_correlator_vanishes_for_product_states():
+    A, B = I.product_sites([0.8, 0.6], [0.28, -0.96])
+    env = O.init_env(A, B, 4)
+    sz = np.diag([0.5, -0.5])
+    S = O.row_correlator(env, A, B, sz, sz, 5)
+    assert np.all(np.abs(S) < 1e-15)
+
+
+def test_ising_row_correlator_decays_and_starts_at_onsager():
+    beta = 0.40
+    A, W = I.ising_peps(beta)
+    env = O.init_env(A, A, 16)
+    O.converge(env, A, A, 16, 16, "standard", max_iter=40, tol=1e-13)
+    sz = np.diag([1.0, -1.0])
+    S = O.row_correlator(env, A, A, sz, sz, 8)
+    assert abs(S[0] - ON.nn_correlation(beta)) < 2e-4   # m = 0 at beta < beta_c
+    assert np.all(np.diff(S) < 0) and S[-1] > 0
