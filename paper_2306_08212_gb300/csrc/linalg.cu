@@ -549,65 +549,82 @@ cudaError_t normalize_f64(cudaStream_t s, double* x, long long n, double* scratc
 // (shifted CholeskyQR: Fukaya, Kannan, Nakatsukasa, Yamamoto & Yanagisawa,
 // SIAM J. Sci. Comput. 42, A477 (2020)), and a strided copy.
 // ---------------------------------------------------------------------------
-// One warp: lane i holds row i of the (<= 32 x 32) diagonal block in registers;
-// right-looking Cholesky with shuffles, then lane j forms column j of the
-// inverse by forward substitution.
-__global__ void __launch_bounds__(32)
+// One block of 128 threads (all four schedulers of the SM, whose FP64 pipes are
+// narrow): right-looking Cholesky of the (<= 32 x 32) diagonal block in shared
+// memory -- one thread takes the pivot, the column scaling and the rank-1
+// update of the trailing triangle are spread over the block -- then the
+// inverse row by row, x_i = (e_i - sum_k L_ik x_k) / L_ii, with the sum over k
+// split into four partial sums per column.
+constexpr int kCholThreads = 128;
+
+__global__ void __launch_bounds__(kCholThreads)
 chol_diag_kernel(double* __restrict__ G, int lda, int j0, int jb, double* __restrict__ Linv,
                  double floor, int* floored, double tau, int* __restrict__ defmask) {
-  const int lane = threadIdx.x;
-  double a[32];
-  double rinv[32];  // 1 / L[k][k], reused by the inverse (one division per pivot)
-#pragma unroll
-  for (int j = 0; j < 32; ++j)
-    a[j] = (lane < jb && j < jb && j <= lane) ? G[(long long)(j0 + lane) * lda + j0 + j] : 0.0;
-#pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    if (k < jb) {
-      double dkk = __shfl_sync(0xffffffffu, a[k], k);
-      int def = 0;
+  __shared__ double L[32][33];
+  __shared__ double X[32][33];
+  __shared__ double rinv[32];
+  __shared__ double part[4][32];
+  __shared__ int s_def;
+  const int t = threadIdx.x;
+  for (int e = t; e < 32 * 32; e += kCholThreads) {
+    const int i = e / 32, j = e % 32;
+    L[i][j] = (i < jb && j < jb && j <= i) ? G[(long long)(j0 + i) * lda + j0 + j] : 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < jb; ++k) {
+    if (t == 0) {
+      double dkk = L[k][k];
+      s_def = 0;
       if (defmask && !(dkk > tau)) {  // column k lies in the span of the earlier ones
-        def = 1;
+        s_def = 1;
+        defmask[j0 + k] = 1;
         dkk = 1.0;
       } else if (!(dkk > floor)) {
         dkk = floor;
-        if (lane == 0) atomicAdd(floored, 1);
+        atomicAdd(floored, 1);
       }
-      if (def && lane == 0) defmask[j0 + k] = 1;
       const double piv = sqrt(dkk);
-      const double rp = 1.0 / piv;
-      rinv[k] = rp;
-      if (lane == k) a[k] = piv;
-      if (lane > k) a[k] = def ? 0.0 : a[k] * rp;
-      const double lk = a[k];  // L[lane][k]
-#pragma unroll
-      for (int j = k + 1; j < 32; ++j) {
-        const double ljk = __shfl_sync(0xffffffffu, lk, j);  // L[j][k]
-        if (j < jb && j <= lane) a[j] -= lk * ljk;
-      }
+      L[k][k] = piv;
+      rinv[k] = 1.0 / piv;
     }
+    __syncthreads();
+    const int m = jb - k - 1;  // rows below the pivot
+    if (t < m) L[k + 1 + t][k] = s_def ? 0.0 : L[k + 1 + t][k] * rinv[k];
+    __syncthreads();
+    // trailing triangle: (i, j) with k < j <= i < jb
+    for (int e = t; e < m * m; e += kCholThreads) {
+      const int i = k + 1 + e / m, j = k + 1 + e % m;
+      if (j <= i) L[i][j] -= L[i][k] * L[j][k];
+    }
+    __syncthreads();
   }
-  if (lane < jb) {
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (j < jb) G[(long long)(j0 + lane) * lda + j0 + j] = (j <= lane) ? a[j] : 0.0;
+  for (int e = t; e < jb * jb; e += kCholThreads) {
+    const int i = e / jb, j = e % jb;
+    G[(long long)(j0 + i) * lda + j0 + j] = (j <= i) ? L[i][j] : 0.0;
   }
-  // X = L^{-1}: lane j keeps column j; row i needs L[i][k] (k < i) from lane i
-  double x[32];
-#pragma unroll
+  // inverse: thread t handles column j = t % 32 and quarter q = t / 32 of the k range
+  const int jc = t % 32, q = t / 32;
   for (int i = 0; i < 32; ++i) {
-    double acc = (i == lane) ? 1.0 : 0.0;
-#pragma unroll
-    for (int k = 0; k < i; ++k) acc -= __shfl_sync(0xffffffffu, a[k], i) * x[k];
-    x[i] = (i < jb) ? acc * rinv[i] : 0.0;
+    double acc = 0.0;
+    for (int k = q; k < i; k += 4) acc -= L[i][k] * X[k][jc];
+    part[q][jc] = acc;
+    __syncthreads();
+    if (q == 0)
+      X[i][jc] = (i < jb && jc <= i)
+                     ? ((i == jc ? 1.0 : 0.0) + part[0][jc] + part[1][jc] + part[2][jc] +
+                        part[3][jc]) * rinv[i]
+                     : 0.0;
+    __syncthreads();
   }
-#pragma unroll
-  for (int i = 0; i < 32; ++i) Linv[i * 32 + lane] = (i < jb && lane < jb) ? x[i] : 0.0;
+  for (int e = t; e < 32 * 32; e += kCholThreads) {
+    const int i = e / 32, j = e % 32;
+    Linv[i * 32 + j] = (i < jb && j < jb) ? X[i][j] : 0.0;
+  }
 }
 
 cudaError_t chol_diag(cudaStream_t s, double* G, int lda, int j0, int jb, double* Linv,
                       double floor, int* floored, double tau, int* defmask) {
-  chol_diag_kernel<<<1, 32, 0, s>>>(G, lda, j0, jb, Linv, floor, floored, tau, defmask);
+  chol_diag_kernel<<<1, kCholThreads, 0, s>>>(G, lda, j0, jb, Linv, floor, floored, tau, defmask);
   return cudaGetLastError();
 }
 
