@@ -49,14 +49,17 @@ def parse():
 # ---------------------------------------------------------------------------
 # distributed helpers (one process per GPU; independent replicas)
 # ---------------------------------------------------------------------------
-def dist_setup(n):
+def dist_setup(n, backend="nccl"):
+    """(rank, world, dist) for N > 1 under torchrun (one process per GPU), else (0, 1, None).
+    The ranks are independent replicas: the process group carries only the barriers around the
+    timed region and the max-over-ranks reduction of its duration."""
     import torch
     if n <= 1 or "RANK" not in os.environ:
         return 0, 1, None
     import torch.distributed as dist
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist.init_process_group("nccl")
+    if backend == "nccl":
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dist.init_process_group(backend)
     return dist.get_rank(), dist.get_world_size(), dist
 
 
@@ -69,9 +72,22 @@ def max_over_ranks(dist, v):
     if dist is None:
         return v
     import torch
-    t = torch.tensor([v], device="cuda", dtype=torch.float64)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], device=dev, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(moves_per_rank, world, seconds_max):
+    """Whole-job moves/s: the moves of all ranks over the slowest rank's time (weak scaling)."""
+    return moves_per_rank * world / seconds_max
+
+
+def bench_config(args, world):
+    return {"workload": WORKLOAD.replace("D=8", f"D={args.D}").replace("chi=256", f"chi={args.chi}")
+                                .replace("chi'=256", f"chi'={args.chi}"),
+            "precision": args.precision, "parallelism": f"replicas{world}",
+            "l2": "working set > L2 (no flush)"}
 
 
 # ---------------------------------------------------------------------------
@@ -267,8 +283,7 @@ def _run_native(args):
         env.free()
         return None
     peaks, peaks_kind = measured_peaks()
-    moves = 4 * args.steps * world
-    value = moves / t
+    value = job_throughput(4 * args.steps, world, t)
     roof = roofline(args, stats, peaks, peaks_kind)
     line = {
         "metric": "CTM moves/s at D=8 chi=256: reduced-sequential mixed precision (vs FP64 standard)",
@@ -283,13 +298,13 @@ def _run_native(args):
         "vs_baseline": None,
         "dtype": {"fp64": "f64", "tf32": "tf32/f32acc+f64", "bf16": "bf16/f32acc+f64"}[args.precision],
         "data": "synthetic: A,B ~ N(0,1) unit norm, seeds 0/1",
-        "config": {"workload": WORKLOAD.replace("D=8", f"D={args.D}").replace("chi=256", f"chi={args.chi}"),
-                   "precision": args.precision, "parallelism": f"replicas{world}",
-                   "l2": "working set > L2 (no flush)"},
-        "e2e": {"value": moves / t_e2e, "unit": "moves/s", "h2d_bytes_per_step": h2d,
+        "config": bench_config(args, world),
+        "e2e": {"value": job_throughput(4 * args.steps, world, t_e2e), "unit": "moves/s",
+                "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "kernel_classes": {k["name"]: {"launches": k["count"], "ms_per_step": k["ms"]}
+        "kernel_classes": {k["name"]: {"launches": k["count"], "ms_per_step": k["ms"],
+                                       "gflop_per_step": k["flops"] / 1e9}
                            for k in breakdown},
         "clocks": clk,
         "roofline": roof,
@@ -323,6 +338,13 @@ def time_standard(args, A, B, host_env):
     return {"value": 1.0 / t, "unit": "moves/s", "moves_timed": 1, "dtype": "f64"}
 
 
+# DRAM bytes (read + write) per launch from one ncu capture of each class on this workload
+# (profiles/gemm_f64_d8_chi256_bf16_step.md: mean of three 16x16-tile launches;
+# profiles/tc_gemm_d8_chi256_bf16_step.md: mean of three BN=256 launches).  Stale, and to be
+# set to None, as soon as the kernel changes.
+TRAFFIC_PER_LAUNCH = {"gemm_f64": 1.843e6, "tc_bf16_gemm": 9.25e6}
+
+
 def roofline(args, stats, peaks, peaks_kind):
     if not stats:
         return None
@@ -340,7 +362,9 @@ def roofline(args, stats, peaks, peaks_kind):
     else:
         peak, bound, note = fp64_gemm_peak(), "alu", "fp64: cuBLAS DGEMM measured here"
     return {"kernel": top["name"], "bound": bound, "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": (TRAFFIC_PER_LAUNCH.get(top["name"])
+                        if (args.D, args.chi, args.precision) == (D_, CHI, "bf16") else None),
             "launches": top["count"], "avg_launch_us": avg_s * 1e6, "peak_source": note}
 
 
@@ -385,9 +409,9 @@ def run_reference(args):
           "sample": "one reduced-sequential column absorption per step at the bench shapes"}
     return {"impl": "reference",
             "metric": "CTM moves/s at D=8 chi=256: reduced-sequential mixed precision (vs FP64 standard)",
-            "value": value, "unit": "moves/s", "n_gpus": 1, "steps": args.steps,
+            "value": value, "unit": "moves/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
-            "config": {"workload": WORKLOAD}, "cpu_baseline": cb,
+            "config": bench_config(args, args.gpus), "cpu_baseline": cb,
             "e2e": {"value": value, "unit": "moves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
