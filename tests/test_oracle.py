@@ -10,6 +10,9 @@
 * The Ising-norm PEPS reproduces Onsager's free energy and nearest-neighbour
   correlation and Yang's magnetisation.
 * Four quarter turns of a site are the identity.
+* With v_l, v_r keeping the whole range of their boundary columns, the one-row
+  reduced network equals the reduced-environment network written out as one
+  einsum (Sec. III, Appendix).
 """
 import numpy as np
 import pytest
@@ -240,3 +243,33 @@ def test_ising_row_correlator_decays_and_starts_at_onsager():
     S = O.row_correlator(env, A, A, sz, sz, 8)
     assert abs(S[0] - ON.nn_correlation(beta)) < 2e-4   # m = 0 at beta < beta_c
     assert np.all(np.diff(S) < 0) and S[-1] > 0
+
+
+def _reduced_env_network(env, A):
+    """Q[alpha, X_ket, X_bra, beta] of Sec. III written out as one network: the
+    upper-left quadrant {C1_a, T2_a, T1_a; A (ket), A (bra)} closed on the right by
+    {C2_a, T3_a}, legs as documented (C1[down,right], C2[left,down],
+    T[prev, ket, bra, next]; site (p, u, l, d, r))."""
+    return np.einsum("dg,gUVe,aLMd,pULXR,pVMYS,ez,zRSw->aXYw",
+                     env[("C", 1, "a")], env[("T", 2, "a")], env[("T", 1, "a")], A, A,
+                     env[("C", 2, "a")], env[("T", 3, "a")], optimize=True)
+
+
+@pytest.mark.parametrize("chi_env,chip", [(4, HUGE), (4, 8), (5, 15)])
+def test_reduced_network_is_the_reduced_environment_when_v_l_v_r_keep_their_range(chi_env, chip):
+    """Appendix, Fig. 8 and Fig. 3c: v_l, v_r only compress the left and right
+    boundary columns.  When they keep the whole range of L = C1 T1 and R = C2 T3
+    (chi' >= chi D, chi >= the environment's chi) the one-row network
+    M = C'1 T'2 C'2 equals the reduced-environment network of Sec. III entry by
+    entry, whatever basis the factorisations return."""
+    D = 2 if chi_env == 4 else 3
+    A, B = I.random_sites(2, D, 31)
+    env = I.random_env_tensors(D, chi_env, seed=5)
+    sites = {"a": A, "b": B}
+    M = O.reduced_network(O.View(env, 0), "a", sites, chi_env, chip)
+    Q = _reduced_env_network(env, A)
+    assert M.shape == Q.shape
+    np.testing.assert_allclose(M, Q, rtol=0, atol=1e-12 * np.abs(Q).max())
+    # a planted mistake: the sites of the two sublattices exchanged
+    Mb = O.reduced_network(O.View(env, 0), "a", {"a": B, "b": A}, chi_env, chip)
+    assert np.abs(Mb - Q).max() > 1e-3 * np.abs(Q).max()
