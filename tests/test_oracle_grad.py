@@ -1,0 +1,139 @@
+"""Pins of the gradient oracle (oracle/ctm_grad.py) against facts outside it.
+
+* Its forward pass is the (separately pinned) numpy oracle's reduced-sequential
+  iteration: same energy to 1e-12.
+* The hand-written adjoint of the truncated SVD equals central finite
+  differences and PyTorch's own SVD backward on gauge-invariant functions of the
+  kept left vectors, for tall and wide matrices, and stays finite and correct
+  when kept singular values are degenerate (the Lorentzian broadening).
+* The gradient of the energy after CTM iterations equals central finite
+  differences (h = 1e-6) of the numpy oracle's energy on 64 entries of A and B.
+
+The exactness pins run the adjoint with a vanishing broadening (EXACT): the
+Lorentzian term shifts every pair whose squared relative gap is near eps, and
+the spectra of a CTM move have such pairs among small kept values.  The
+broadened adjoint (eps = 1e-12 relative to s_max^4) is pinned on degenerate
+spectra, where the exact one divides by zero, and its bias on the energy
+gradient is bounded.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import ctm_grad as G  # noqa: E402
+from oracle import ctm_oracle as O  # noqa: E402
+from paper_2306_08212_gb300 import inputs as I  # noqa: E402
+
+EXACT = 1e-40  # broadening small enough to leave every non-degenerate pair exact
+
+
+def _np_energy(env0, A, B, chi, iters):
+    env = {k: v.copy() for k, v in env0.items()}
+    for _ in range(iters):
+        for d in O.MOVE_ORDER:
+            O.move(env, d, A, B, chi, chi, "reduced_sequential")
+    H = O.heisenberg_bond()
+    return float(np.mean([O.expect_bond(env, A, B, b, H) for b in range(4)]))
+
+
+def _setup(D=2, chi=6, seed=3):
+    A, B = I.random_sites(2, D, seed)
+    env0 = O.init_env(A, B, chi)
+    return A, B, env0
+
+
+def test_forward_is_the_numpy_oracle():
+    A, B, env0 = _setup()
+    for iters in (1, 2):
+        e_np = _np_energy(env0, A, B, 6, iters)
+        e_t = float(G.energy(env0, torch.tensor(A), torch.tensor(B), 6, iters))
+        assert abs(e_t - e_np) < 1e-12
+
+
+def _projector_loss(Uk, W):
+    return torch.sum(W * (Uk @ Uk.T))  # depends on span(Uk) only
+
+
+@pytest.mark.parametrize("shape,k", [((12, 7), 3), ((6, 10), 4), ((9, 9), 5)])
+def test_truncated_svd_adjoint(shape, k):
+    rng = np.random.default_rng(7)
+    M0 = rng.standard_normal(shape)
+    W = torch.tensor(rng.standard_normal((shape[0], shape[0])))
+    M = torch.tensor(M0, requires_grad=True)
+    g = torch.autograd.grad(_projector_loss(G.TruncatedLeft.apply(M, k, EXACT), W), M)[0].numpy()
+    # PyTorch's own SVD backward (non-degenerate spectrum)
+    M2 = torch.tensor(M0, requires_grad=True)
+    U = torch.linalg.svd(M2, full_matrices=False)[0][:, :k]
+    g_lib = torch.autograd.grad(_projector_loss(U, W), M2)[0].numpy()
+    np.testing.assert_allclose(g, g_lib, rtol=0, atol=1e-10 * np.abs(g_lib).max())
+    # central differences
+    h = 1e-6
+    fd = np.zeros_like(M0)
+    for i in range(shape[0]):
+        for j in range(shape[1]):
+            Mp, Mm = M0.copy(), M0.copy()
+            Mp[i, j] += h
+            Mm[i, j] -= h
+            fp = _projector_loss(G.TruncatedLeft.apply(torch.tensor(Mp), k, EXACT), W)
+            fm = _projector_loss(G.TruncatedLeft.apply(torch.tensor(Mm), k, EXACT), W)
+            fd[i, j] = float(fp - fm) / (2 * h)
+    np.testing.assert_allclose(g, fd, rtol=0, atol=1e-7 * np.abs(fd).max())
+
+
+def test_degenerate_kept_singular_values():
+    """s = (3, 2, 2, 1, 0.5) with k = 3: the kept pair is degenerate, the cut is not.
+    The projector onto the kept span is smooth, its gradient finite; F without
+    broadening would divide by zero."""
+    rng = np.random.default_rng(11)
+    Q1, _ = np.linalg.qr(rng.standard_normal((8, 5)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((5, 5)))
+    M0 = Q1 @ np.diag([3.0, 2.0, 2.0, 1.0, 0.5]) @ Q2.T
+    W = torch.tensor(rng.standard_normal((8, 8)))
+    M = torch.tensor(M0, requires_grad=True)
+    g = torch.autograd.grad(_projector_loss(G.TruncatedLeft.apply(M, 3, 1e-12), W), M)[0].numpy()
+    assert np.all(np.isfinite(g))
+    h = 1e-6
+    fd = np.zeros_like(M0)
+    for i in range(8):
+        for j in range(5):
+            Mp, Mm = M0.copy(), M0.copy()
+            Mp[i, j] += h
+            Mm[i, j] -= h
+            fp = _projector_loss(G.TruncatedLeft.apply(torch.tensor(Mp), 3, 1e-12), W)
+            fm = _projector_loss(G.TruncatedLeft.apply(torch.tensor(Mm), 3, 1e-12), W)
+            fd[i, j] = float(fp - fm) / (2 * h)
+    np.testing.assert_allclose(g, fd, rtol=0, atol=1e-6 * np.abs(fd).max())
+
+
+def test_energy_gradient_matches_central_differences():
+    """D=2, chi=6: all 32 entries of A and all 32 of B (64 in total), one iteration."""
+    A, B, env0 = _setup()
+    chi, iters = 6, 1
+    _, gA, gB = G.energy_and_grad(env0, A, B, chi, iters, eps=EXACT)
+    h = 1e-6
+    for X, g, which in ((A, gA, "A"), (B, gB, "B")):
+        fd = np.zeros_like(X)
+        for idx in np.ndindex(X.shape):
+            Xp, Xm = X.copy(), X.copy()
+            Xp[idx] += h
+            Xm[idx] -= h
+            if which == "A":
+                ep, em = _np_energy(env0, Xp, B, chi, iters), _np_energy(env0, Xm, B, chi, iters)
+            else:
+                ep, em = _np_energy(env0, A, Xp, chi, iters), _np_energy(env0, A, Xm, chi, iters)
+            fd[idx] = (ep - em) / (2 * h)
+        np.testing.assert_allclose(g, fd, rtol=0, atol=1e-6 * np.abs(fd).max())
+    # the energy does not change when A is scaled, so dE/dA is orthogonal to A
+    assert abs(np.sum(gA * A)) < 1e-9 * np.abs(gA).max()
+
+
+def test_broadened_energy_gradient_stays_close():
+    """With eps = 1e-12 the energy gradient differs from the exact one only through
+    pairs of kept singular values whose squared relative gap is near eps."""
+    A, B, env0 = _setup()
+    _, gA0, gB0 = G.energy_and_grad(env0, A, B, 6, 1, eps=EXACT)
+    _, gA1, gB1 = G.energy_and_grad(env0, A, B, 6, 1, eps=1e-12)
+    assert np.all(np.isfinite(gA1)) and np.all(np.isfinite(gB1))
+    scale = max(np.abs(gA0).max(), np.abs(gB0).max())
+    assert max(np.abs(gA1 - gA0).max(), np.abs(gB1 - gB0).max()) < 5e-2 * scale
