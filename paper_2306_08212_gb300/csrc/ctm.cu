@@ -1347,33 +1347,56 @@ double scalar_of(ctm_ctx* c, const Ten& t) {
   return v;
 }
 
+// Two-site density matrix of the horizontal bond (x, y) in frame r, from the
+// 2 x 4 window (Sec. II, Fig. 1d): left half {C1, T2, T1, C4, T4; x} and right
+// half {T2, C2, T3, C3, T4; y}, each with its physical legs open.  The site's
+// ket and bra layers enter one after the other (the sequential order of Sec. IV)
+// instead of as the double-layer tensor, so the largest intermediate is
+// chi^2 d^2 D^4 rather than chi^2 D^6 (137 GB at D = 8, chi = 256).  The long
+// chi^2 side of each contraction is its column side (grid x of the GEMM).
 double expect_bond(ctm_ctx* c, int bond, const double* op_host) {
   const int r = (bond >= 2) ? 1 : 0;
   const int x = bond & 1, y = other(x);
-  const int d = c->d, D2 = c->D * c->D;
+  const int d = c->d, D = c->D, D2 = D * D;
   Ten Sx, Sy;
   site(c, r, x, Sx);
   site(c, r, y, Sy);
-  Tmp ax = ein64(c, "puldr,PULDR->pPuUlLdDrR", Sx, Sx);
-  Tmp ay = ein64(c, "puldr,PULDR->pPuUlLdDrR", Sy, Sy);
-  Ten axv = view(ax.t, {d, d, D2, D2, D2, D2}), ayv = view(ay.t, {d, d, D2, D2, D2, D2});
-  Tmp left;
+  Tmp left;  // [e, (R_ket R_bra), k, p, P]
   {
-    Tmp e1 = ein64(c, "dg,gUe->dUe", E(c, 0, 1, x, r), edge_fused(E(c, 1, 2, x, r)));
-    Tmp e2 = ein64(c, "dUe,mLd->mLUe", e1, edge_fused(E(c, 1, 1, x, r)));
-    Tmp e3 = ein64(c, "mLUe,lm->lLUe", e2, E(c, 0, 4, x, r));
-    Tmp e4 = ein64(c, "lLUe,kXl->kXLUe", e3, edge_fused(E(c, 1, 4, x, r)));
-    left = ein64(c, "kXLUe,pPULXR->eRkpP", e4, axv);
+    Tmp s2;  // [P, X_bra, R_bra, p, X_ket, R_ket, m, e]
+    {
+      Tmp s1;  // [p, X_ket, R_ket, m, L_bra, U_bra, e]
+      {
+        Tmp e1 = ein64(c, "dg,gUe->dUe", E(c, 0, 1, x, r), edge_fused(E(c, 1, 2, x, r)));
+        Tmp e2 = ein64(c, "dUe,mLd->mLUe", e1, edge_fused(E(c, 1, 1, x, r)));
+        const Ten& t = e2.t;
+        s1 = ein64(c, "pcagh,mabcfe->pghmbfe", Sx, view(t, {t.dims[0], D, D, D, D, t.dims[3]}));
+      }
+      s2 = ein64(c, "Pfbij,pghmbfe->Pijpghme", Sx, s1);
+    }
+    Tmp bl = ein64(c, "kXl,lm->kXm", edge_fused(E(c, 1, 4, x, r)), E(c, 0, 4, x, r));
+    const Ten& b = bl.t;
+    left = ein64(c, "Pijpghme,kgim->ehjkpP", s2, view(b, {b.dims[0], D, D, b.dims[2]}));
   }
-  Tmp right;
+  Tmp right;  // [e, (L_ket L_bra), k, q, Q]
   {
-    Tmp f1 = ein64(c, "eVz,zh->eVh", edge_fused(E(c, 1, 2, y, r)), E(c, 0, 2, y, r));
-    Tmp f2 = ein64(c, "eVh,hWt->eVWt", f1, edge_fused(E(c, 1, 3, y, r)));
-    Tmp f3 = ein64(c, "eVWt,ti->eVWi", f2, E(c, 0, 3, y, r));
-    Tmp f4 = ein64(c, "eVWi,iYk->eVWYk", f3, edge_fused(E(c, 1, 4, y, r)));
-    right = ein64(c, "eVWYk,qQVRYW->eRkqQ", f4, ayv);
+    Tmp s2;  // [Q, L_bra, Y_bra, q, L_ket, Y_ket, e, t]
+    {
+      Tmp s1;  // [q, L_ket, Y_ket, e, V_bra, W_bra, t]
+      {
+        Tmp f1 = ein64(c, "eVz,zh->eVh", edge_fused(E(c, 1, 2, y, r)), E(c, 0, 2, y, r));
+        Tmp f2 = ein64(c, "eVh,hWt->eVWt", f1, edge_fused(E(c, 1, 3, y, r)));
+        const Ten& t = f2.t;
+        s1 = ein64(c, "qaghc,eabcft->qghebft", Sy, view(t, {t.dims[0], D, D, D, D, t.dims[3]}));
+      }
+      s2 = ein64(c, "Qbnmf,qghebft->Qnmqghet", Sy, s1);
+    }
+    Tmp br = ein64(c, "ti,iYk->tYk", E(c, 0, 3, y, r), edge_fused(E(c, 1, 4, y, r)));
+    const Ten& b = br.t;
+    right = ein64(c, "Qnmqghet,thmk->egnkqQ", s2, view(b, {b.dims[0], D, D, b.dims[2]}));
   }
-  Tmp rho = ein64(c, "eRkpP,eRkqQ->pqPQ", left, right);
+  Tmp rho = ein64(c, "eRkpP,eRkqQ->pqPQ", view(left.t, {left.t.dims[0], D2, left.t.dims[3], d, d}),
+                  view(right.t, {right.t.dims[0], D2, right.t.dims[3], d, d}));
   Ten rv = view(rho.t, {d * d, d * d});
   Tmp op(c, {d * d, d * d});
   ck(cudaMemcpyAsync(op.t.p, op_host, sizeof(double) * d * d * d * d, cudaMemcpyHostToDevice,
