@@ -186,6 +186,29 @@ int ctm_singular_values_noalloc(const double* M, int rows, int cols, double* s,
                                 void* stream);
 
 /*
+ * Adjoint of the truncated left singular vectors that define a projector (the
+ * factorisations of Sec. IV, Fig. 4a, and of the Appendix, differentiated).
+ * Inputs, all device memory on the current device, FP64, row-major:
+ *   U  rows x r, s r (descending), Vt r x cols -- a thin SVD M = U diag(s) Vt,
+ *      r = min(rows, cols);
+ *   gU rows x k -- the gradient of a loss with respect to the leading k columns
+ *      of U (1 <= k <= r);
+ *   eps -- Lorentzian broadening relative to s[0]^4 (e.g. 1e-12; 0 = none).
+ * Output gM (rows x cols, caller-allocated):
+ *   gM = U [(F o (J - J^T)) diag(s)] Vt + (I - U U^T) gU diag(s_k)^-1 Vt_k,
+ *   J = U^T gU (gU zero-padded to r columns), F_ij = E_ij / (E_ij^2 + eps s_0^4),
+ *   E_ij = s_j^2 - s_i^2, F_ii = 0 (Liao, Liu, Wang & Xiang 2019; the second
+ *   term, Townsend 2016, vanishes when rows <= cols).
+ * s and Vt receive no gradient (a projector v v^T uses the left vectors only).
+ * Stream-ordered on `stream` (a cudaStream_t); temporaries come from the
+ * stream-ordered pool; no synchronisation.  Inputs are not modified.
+ * Errors: CTM_ERR_ARG (null pointer, k outside [1, r], eps < 0), CTM_ERR_OOM,
+ * CTM_ERR_CUDA.
+ */
+int ctm_svd_left_adjoint(const double* U, const double* s, const double* Vt, const double* gU,
+                         int rows, int cols, int k, double eps, double* gM, void* stream);
+
+/*
  * Test hook for the contraction kernels: C = A B for host row-major A (M x K),
  * B (K x N), C (M x N), computed on the current device in `precision`
  * (CTM_FP64: the FP64 leg-map kernel; CTM_TF32 / CTM_BF16: the tcgen05 kernel

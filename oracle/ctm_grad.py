@@ -64,20 +64,26 @@ class TruncatedLeft(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g):
         U, S, Vh, sign = ctx.saved_tensors
-        k, eps = ctx.k, ctx.eps
-        m, r = U.shape
-        gU = torch.zeros_like(U)
-        gU[:, :k] = g * sign
-        J = U.T @ gU
-        E = S[None, :] ** 2 - S[:, None] ** 2          # E_ij = s_j^2 - s_i^2
-        F = E / (E * E + eps * S[0] ** 4)                # eps relative to s_max^4
-        F.fill_diagonal_(0.0)
-        inner = (F * (J - J.T)) * S[None, :]             # (F o skew) S
-        gM = U @ inner @ Vh
-        if m > r:  # part of dU outside span(U); only the kept columns are non-zero
-            gperp = gU - U @ J
-            gM = gM + (gperp[:, :k] / S[None, :k]) @ Vh[:k, :]
-        return gM, None, None
+        return svd_left_adjoint(U, S, Vh, g * sign, ctx.eps), None, None
+
+
+def svd_left_adjoint(U, S, Vh, gUk, eps):
+    """dM for M = U diag(S) Vh (thin, S descending) given the gradient gUk of the
+    leading k = gUk.shape[1] columns of U (the formula of the module docstring)."""
+    m, r = U.shape
+    k = gUk.shape[1]
+    gU = torch.zeros_like(U)
+    gU[:, :k] = gUk
+    J = U.T @ gU
+    E = S[None, :] ** 2 - S[:, None] ** 2          # E_ij = s_j^2 - s_i^2
+    F = E / (E * E + eps * S[0] ** 4)                # eps relative to s_max^4
+    F.fill_diagonal_(0.0)
+    inner = (F * (J - J.T)) * S[None, :]             # (F o skew) S
+    gM = U @ inner @ Vh
+    if m > r:  # part of dU outside span(U); only the kept columns are non-zero
+        gperp = gU - U @ J
+        gM = gM + (gperp[:, :k] / S[None, :k]) @ Vh[:k, :]
+    return gM
 
 
 def trunc_left(M, k, eps):

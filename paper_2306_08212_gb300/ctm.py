@@ -46,6 +46,8 @@ SIGNATURES = {
     "ctm_profile_enable": (ctypes.c_int, [_P, ctypes.c_int]),
     "ctm_profile_read": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _D, _D]),
     "ctm_singular_values_noalloc": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _P, _P]),
+    "ctm_svd_left_adjoint": (ctypes.c_int, [_P, _P, _P, _P, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.c_double, _P, _P]),
     "ctm_contract_test": (ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
                                           ctypes.c_longlong, _D, _D, _D]),
     "ctm_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int]),
@@ -235,6 +237,23 @@ def ctm_singular_values_noalloc(M_ptr, rows, cols, s_ptr, stream=None):
     st = stream if stream is not None else _current_stream()
     return load().ctm_singular_values_noalloc(ctypes.c_void_p(M_ptr), int(rows), int(cols),
                                               ctypes.c_void_p(s_ptr), st)
+
+
+def ctm_svd_left_adjoint(U, s, Vt, gU, eps=1e-12, stream=None):
+    """gM for M = U diag(s) Vt from the gradient gU of the leading gU.shape[1] columns of U.
+
+    U, s, Vt, gU: CUDA float64 tensors (or host arrays, copied to the current device).
+    Returns (status, gM) with gM a CUDA tensor of M's shape."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t = [torch.as_tensor(x, dtype=torch.float64, device=dev).contiguous() for x in (U, s, Vt, gU)]
+    rows, cols, k = t[0].shape[0], t[2].shape[1], t[3].shape[1]
+    gM = torch.empty((rows, cols), dtype=torch.float64, device=dev)
+    st = stream if stream is not None else _current_stream()
+    rc = load().ctm_svd_left_adjoint(*(ctypes.c_void_p(x.data_ptr()) for x in t), int(rows),
+                                     int(cols), int(k), float(eps), ctypes.c_void_p(gM.data_ptr()),
+                                     st)
+    return rc, gM
 
 
 def ctm_contract_test(precision, A, B):
