@@ -1,4 +1,4 @@
-"""Batched independent states (config 4 style: different D, chi = 2 D^2) give
+"""Batched independent states (uneven D, chi = 2 D^2) give
 the same results as advancing each state alone."""
 import numpy as np
 import pytest

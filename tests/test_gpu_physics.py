@@ -1,11 +1,11 @@
 """GPU runs checked against exact results and invariants rather than the oracle.
 
-* Ising-norm PEPS (BASELINE config 2): ln Z per site (Onsager), nearest-neighbour
+* Ising-norm PEPS (D=2 per layer): ln Z per site (Onsager), nearest-neighbour
   <s s'> and the magnetisation (Yang), every mode, through ctm_converge.
 * Full-size workload of the bench (d=2, D=8, chi=256) in mixed precision: the
   spectra are descending, non-negative and normalised, energies lie in the
   spectrum of S.S, and BF16 agrees with TF32 to the BF16 error level.
-* Config 3 (D=6, chi=144): TF32 and BF16 errors against the FP64 path, printed.
+* Random D=6, chi=144: TF32 and BF16 errors against the FP64 path, printed.
 """
 import numpy as np
 import pytest
@@ -84,7 +84,7 @@ def test_full_size_bench_workload_properties(ctm):
     assert de < 1e-2 and ds < 5e-2
 
 
-def test_config3_precision_errors_vs_fp64(ctm):
+def test_random_d6_chi144_precision_errors_vs_fp64(ctm):
     A, B = I.random_sites(2, 6, 0)
     H = O.heisenberg_bond()
     res = {}
@@ -100,7 +100,7 @@ def test_config3_precision_errors_vs_fp64(ctm):
     for prec, bound in (("tf32", 1e-3), ("bf16", 1e-2)):
         de = max(abs(a - b) for a, b in zip(res[prec][0], res["fp64"][0]))
         ds = max(np.abs(a[:32] - b[:32]).max() for a, b in zip(res[prec][1], res["fp64"][1]))
-        print(f"config 3 (D=6, chi=144) {prec}: |dE_bond| = {de:.3e}, top-32 spectra {ds:.3e}")
+        print(f"random D=6, chi=144 {prec}: |dE_bond| = {de:.3e}, top-32 spectra {ds:.3e}")
         assert de < bound and ds < 10 * bound
 
 
