@@ -308,6 +308,7 @@ def _run_native(args):
                            for k in breakdown},
         "clocks": clk,
         "roofline": roof,
+        "tensor_cores": tensor_core_util(breakdown, 1e3 * t / args.steps, peaks),
     }
     if std is not None:
         line["fp64_standard"] = std
@@ -336,6 +337,22 @@ def time_standard(args, A, B, host_env):
     t = e0.elapsed_time(e1) / 1e3
     env.free()
     return {"value": 1.0 / t, "unit": "moves/s", "moves_timed": 1, "dtype": "f64"}
+
+
+def tensor_core_util(breakdown, ms_per_step, peaks):
+    """Tensor-core contraction classes of one step: their FLOPs over their own device time
+    against the measured BF16 peak (TF32: x 1.1/2.25, the nominal ratio), and their share of
+    the step's wall time."""
+    out = {}
+    for k in breakdown:
+        if not k["name"].startswith("tc_") or k["ms"] <= 0:
+            continue
+        peak = peaks["bf16_tflops_sustained"] * (1.0 if "bf16" in k["name"] else 1.1 / 2.25)
+        achieved = k["flops"] / (k["ms"] / 1e3) / 1e12
+        out[k["name"]] = {"achieved_tflops": achieved, "peak_tflops": peak,
+                          "frac": achieved / peak, "ms_per_step": k["ms"],
+                          "share_of_step": k["ms"] / ms_per_step}
+    return out
 
 
 # DRAM bytes (read + write) per launch from one ncu capture of each class on this workload

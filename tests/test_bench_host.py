@@ -83,3 +83,21 @@ def test_reference_arm_other_ranks_exit_without_output():
     p = _run_reference(1)
     assert p.returncode == 0, p.stderr
     assert p.stdout.strip() == ""
+
+
+def test_tensor_core_utilisation_from_a_step_breakdown():
+    sys.path.insert(0, ROOT)
+    import bench
+    breakdown = [{"name": "gemm_f64", "count": 10, "ms": 300.0, "flops": 1.2e11},
+                 {"name": "tc_tf32_gemm", "count": 0, "ms": 0.0, "flops": 0.0},
+                 {"name": "tc_bf16_gemm", "count": 528, "ms": 60.0, "flops": 4.5e12},
+                 {"name": "jacobi_f64", "count": 1, "ms": 48.0, "flops": 0.0}]
+    peaks = {"bf16_tflops_sustained": 1720.6}
+    u = bench.tensor_core_util(breakdown, 308.0, peaks)
+    assert list(u) == ["tc_bf16_gemm"]
+    assert u["tc_bf16_gemm"]["achieved_tflops"] == pytest.approx(75.0)
+    assert u["tc_bf16_gemm"]["frac"] == pytest.approx(75.0 / 1720.6)
+    assert u["tc_bf16_gemm"]["share_of_step"] == pytest.approx(60.0 / 308.0)
+    tf = bench.tensor_core_util([{"name": "tc_tf32_gemm", "count": 1, "ms": 1.0, "flops": 1e9}],
+                                10.0, peaks)
+    assert tf["tc_tf32_gemm"]["peak_tflops"] == pytest.approx(1720.6 * 1.1 / 2.25)
