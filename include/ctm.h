@@ -97,22 +97,26 @@ int ctm_converge(ctm_ctx* ctx, int mode, int max_iter, double tol,
 
 /*
  * <op> on one nearest-neighbour bond from the 2-site reduced density matrix of
- * the environment: bond 0 = a left of b, 1 = b left of a, 2 = a above b,
- * 3 = b above a.  op is host, row-major (d*d) x (d*d) with rows and columns
- * ordered (first site, second site).  The result is written to *value (host).
+ * the environment (the 2 x 4 window of Sec. II, Fig. 1d; e.g. the Heisenberg
+ * bond of Eq. 1 that Sec. V evaluates): bond 0 = a left of b, 1 = b left of a,
+ * 2 = a above b, 3 = b above a.  op is host, row-major (d*d) x (d*d) with rows
+ * and columns ordered (first site, second site).  The result is written to
+ * *value (host).  The ket and bra layers of each site enter one after the other
+ * (the order of Sec. IV), so the largest intermediate is chi^2 d^2 D^4 doubles.
  */
 int ctm_expect_bond(ctm_ctx* ctx, int bond, const double* op, double* value);
 
 /*
  * Singular values of corner `corner` (0..7 = C1a, C1b, C2a, C2b, C3a, C3b,
- * C4a, C4b), descending and scaled to sum s^2 = 1.  s is a host buffer of at
- * least chi entries; *len receives the count written.
+ * C4a, C4b), descending and scaled to sum s^2 = 1 (the corner spectra whose
+ * change decides convergence, Sec. II).  s is a host buffer of at least chi
+ * entries; *len receives the count written.
  */
 int ctm_corner_spectrum(ctm_ctx* ctx, int corner, double* s, int* len);
 
 /*
- * All 8 corner spectra at once (same order and scaling as ctm_corner_spectrum),
- * with one batched Jacobi launch when the corners share a shape.  s is a host
+ * All 8 corner spectra at once (same order and scaling as ctm_corner_spectrum;
+ * Sec. II), with one batched Jacobi launch when the corners share a shape.  s is a host
  * buffer of 8 * maxlen doubles (row i = corner i); lens[8] receives the counts.
  */
 int ctm_corner_spectra(ctm_ctx* ctx, double* s, int maxlen, int* lens);
@@ -128,32 +132,36 @@ int ctm_correlator(ctm_ctx* ctx, const double* op1, const double* op2, int xmax,
 
 /*
  * Per-site log norm ln kappa = (1/4) ln[Z22 Z00 / (Z20 Z02)] from the 2x2
- * window with top-left site a, where Zhw closes the environment around an
+ * window (Sec. II, Fig. 1d) with top-left site a, where Zhw closes the environment around an
  * h x w block of sites (corner and edge normalisations cancel).  For the
  * Ising-norm PEPS this is ln Z / N.
  */
 int ctm_log_kappa(ctm_ctx* ctx, double* value);
 
 /*
- * Copy environment tensor (kind, k, x) to the host buffer `out` (may be NULL
- * to query) and its 2 (corner) or 4 (edge) dims to dims[0..3].
+ * Copy environment tensor (kind, k, x) -- one of the corner and edge tensors
+ * of Sec. II, Fig. 1d -- to the host buffer `out` (may be NULL to query) and its
+ * 2 (corner) or 4 (edge) dims to dims[0..3].
  */
 int ctm_get_tensor(ctm_ctx* ctx, int kind, int k, int x, double* out, int* dims);
 
 /*
- * Overwrite environment tensor (kind, k, x) from a host buffer with the given
- * dims (2 for a corner, 4 for an edge; bond dims at most chi, ket/bra dims D).
+ * Overwrite environment tensor (kind, k, x) (Sec. II, Fig. 1d) from a host
+ * buffer with the given dims (2 for a corner, 4 for an edge; bond dims at most
+ * chi, ket/bra dims D).
  */
 int ctm_set_tensor(ctm_ctx* ctx, int kind, int k, int x, const double* in,
                    const int* dims);
 
-/* Number of kernels this library launched on the context so far. */
+/* Number of kernels this library launched on the context so far.
+ * (Measurement; no counterpart in the paper.) */
 long long ctm_kernel_launches(ctm_ctx* ctx);
 
 /*
- * Per-class kernel timing with CUDA events recorded on the context's stream
- * around every launch of a class (0 = FP64 contraction, 1 = TF32 tensor-core
- * contraction, 2 = BF16 tensor-core contraction, 3 = Jacobi SVD sweep kernel).
+ * Per-class kernel timing (measurement; no counterpart in the paper) with CUDA
+ * events recorded on the context's stream around every launch of a class
+ * (0 = FP64 contraction, 1 = TF32 tensor-core contraction, 2 = BF16 tensor-core
+ * contraction, 3 = Jacobi SVD sweep kernel).
  * ctm_profile_enable(ctx, mask) clears the counters and records the classes
  * whose bit (1 << class) is set in mask; 0 stops.  Changing the mask discards
  * the context's recorded CUDA graphs (they are recaptured with event nodes for
@@ -209,7 +217,7 @@ int ctm_svd_left_adjoint(const double* U, const double* s, const double* Vt, con
                          int rows, int cols, int k, double eps, double* gM, void* stream);
 
 /*
- * Test hook for the contraction kernels: C = A B for host row-major A (M x K),
+ * Test hook for the contraction kernels (no counterpart in the paper): C = A B for host row-major A (M x K),
  * B (K x N), C (M x N), computed on the current device in `precision`
  * (CTM_FP64: the FP64 leg-map kernel; CTM_TF32 / CTM_BF16: the tcgen05 kernel
  * with FP32 accumulation).  Allocates its own device buffers; synchronous.
@@ -234,10 +242,12 @@ int ctm_batch_move(ctm_batch* batch, int dir, int mode);
 const char* ctm_batch_last_error(ctm_batch* batch);
 void ctm_batch_free(ctm_batch* batch);
 
-/* Message of the last failure on ctx ("" if none); valid until the next call. */
+/* Message of the last failure on ctx ("" if none); valid until the next call.
+ * (Bookkeeping; no counterpart in the paper.) */
 const char* ctm_last_error(ctm_ctx* ctx);
 
-/* Release every device and host resource of ctx (NULL is allowed). */
+/* Release every device and host resource of ctx (NULL is allowed).
+ * (Bookkeeping; no counterpart in the paper.) */
 void ctm_free(ctm_ctx* ctx);
 
 #ifdef __cplusplus
