@@ -30,6 +30,7 @@ the singular value decomposition", 2016).  S and V^T receive no
 gradient here because a projector v v^T uses the left vectors only.
 """
 import torch
+import torch.utils.checkpoint
 
 from oracle import ctm_oracle as O
 
@@ -208,14 +209,31 @@ def bond_rdm(env, A, B, r, x):
     return ein("eRkpP,eRkqQ->pqPQ", left, right).reshape(d * d, d * d)
 
 
-def energy(env0, A, B, chi, iters, chip=None, eps=1e-12):
+def _iteration(A, B, chi, chip, eps, keys, *tensors):
+    """One iteration (left, up, right, down) as a function of tensors, for checkpointing."""
+    env = dict(zip(keys, tensors))
+    for direction in O.MOVE_ORDER:
+        move(env, direction, A, B, chi, chip, eps)
+    return tuple(env[k] for k in keys)
+
+
+def energy(env0, A, B, chi, iters, chip=None, eps=1e-12, checkpoint=False):
     """Mean Heisenberg bond energy after `iters` iterations (left, up, right, down)
-    of the reduced-sequential move from the fixed environment env0 (numpy arrays)."""
+    of the reduced-sequential move from the fixed environment env0 (numpy arrays).
+
+    checkpoint=True keeps only each iteration's output environment for the
+    backward pass and recomputes the iteration's intermediates there
+    (torch.utils.checkpoint); the gradient is the same."""
     chip = chi if chip is None else chip
-    env = {key: torch.as_tensor(t, dtype=DT) for key, t in env0.items()}
+    keys = sorted(env0)
+    tensors = tuple(torch.as_tensor(env0[k], dtype=DT) for k in keys)
     for _ in range(iters):
-        for direction in O.MOVE_ORDER:
-            move(env, direction, A, B, chi, chip, eps)
+        if checkpoint:
+            tensors = torch.utils.checkpoint.checkpoint(
+                _iteration, A, B, chi, chip, eps, keys, *tensors, use_reentrant=False)
+        else:
+            tensors = _iteration(A, B, chi, chip, eps, keys, *tensors)
+    env = dict(zip(keys, tensors))
     H = torch.as_tensor(O.heisenberg_bond(), dtype=DT)
     total = 0.0
     for bond, (r, x) in O.BONDS.items():
@@ -224,10 +242,10 @@ def energy(env0, A, B, chi, iters, chip=None, eps=1e-12):
     return total / len(O.BONDS)
 
 
-def energy_and_grad(env0, A, B, chi, iters, chip=None, eps=1e-12):
+def energy_and_grad(env0, A, B, chi, iters, chip=None, eps=1e-12, checkpoint=False):
     """(E, dE/dA, dE/dB) as float and numpy arrays."""
     At = torch.tensor(A, dtype=DT, requires_grad=True)
     Bt = torch.tensor(B, dtype=DT, requires_grad=True)
-    E = energy(env0, At, Bt, chi, iters, chip, eps)
+    E = energy(env0, At, Bt, chi, iters, chip, eps, checkpoint)
     gA, gB = torch.autograd.grad(E, (At, Bt))
     return float(E.detach()), gA.numpy(), gB.numpy()

@@ -137,3 +137,14 @@ def test_broadened_energy_gradient_stays_close():
     assert np.all(np.isfinite(gA1)) and np.all(np.isfinite(gB1))
     scale = max(np.abs(gA0).max(), np.abs(gB0).max())
     assert max(np.abs(gA1 - gA0).max(), np.abs(gB1 - gB0).max()) < 5e-2 * scale
+
+
+def test_checkpointed_iterations_give_the_same_gradient():
+    """Checkpointing each CTM iteration (only its output environment kept, the rest
+    recomputed in the backward pass) changes memory, not the gradient."""
+    A, B, env0 = _setup()
+    e0, gA0, gB0 = G.energy_and_grad(env0, A, B, 6, 2, eps=EXACT)
+    e1, gA1, gB1 = G.energy_and_grad(env0, A, B, 6, 2, eps=EXACT, checkpoint=True)
+    assert e1 == e0
+    np.testing.assert_allclose(gA1, gA0, rtol=0, atol=1e-13 * np.abs(gA0).max())
+    np.testing.assert_allclose(gB1, gB0, rtol=0, atol=1e-13 * np.abs(gB0).max())
