@@ -123,6 +123,39 @@ def absorb_edge_seq(T, S, vp1, vp2, vn1, vn2):
     return ein("oeyOQ,eQx->xoOy", X5, vp2)
 
 
+def contract_adjoint(spec, A, B, gC):
+    """(dA, dB) for C = einsum(spec, A, B) given dC: each is one more pairwise
+    contraction, of dC with the other operand (every index of A and B appears in
+    exactly two of A, B, C, as in every contraction of the move)."""
+    ins, out = spec.split("->")
+    a, b = ins.split(",")
+    return ein(f"{out},{b}->{a}", gC, B), ein(f"{a},{out}->{b}", A, gC)
+
+
+ABSORB_SEQ_SPECS = ("AkbB,Bnc->Akbnc", "Akbnc,skoqn->Abcsoq", "Abcsoq,Aqe->bcsoe",
+                    "bcsoe,cNy->bsoeNy", "bsoeNy,sbOQN->oeyOQ", "oeyOQ,eQx->xoOy")
+
+
+def absorb_edge_seq_adjoint(T, S, vp1, vp2, vn1, vn2, gOut):
+    """Hand-written reverse pass of absorb_edge_seq (Sec. IV, Fig. 4b): the six
+    contractions recomputed, then walked backwards with contract_adjoint.  Returns
+    (dT, dS, dvp1, dvp2, dvn1, dvn2); S enters twice (ket and bra), so dS is the sum
+    of both uses."""
+    sp = ABSORB_SEQ_SPECS
+    X1 = ein(sp[0], T, vn1)
+    X2 = ein(sp[1], X1, S)
+    X3 = ein(sp[2], X2, vp1)
+    X4 = ein(sp[3], X3, vn2)
+    X5 = ein(sp[4], X4, S)
+    gX5, gvp2 = contract_adjoint(sp[5], X5, vp2, gOut)
+    gX4, gS_bra = contract_adjoint(sp[4], X4, S, gX5)
+    gX3, gvn2 = contract_adjoint(sp[3], X3, vn2, gX4)
+    gX2, gvp1 = contract_adjoint(sp[2], X2, vp1, gX3)
+    gX1, gS_ket = contract_adjoint(sp[1], X1, S, gX2)
+    gT, gvn1 = contract_adjoint(sp[0], T, vn1, gX1)
+    return gT, gS_ket + gS_bra, gvp1, gvp2, gvn1, gvn2
+
+
 def compose(v1, v2):
     return ein("akc,cby->akby", v1, v2)
 
