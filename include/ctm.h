@@ -187,7 +187,9 @@ int ctm_profile_read(ctm_ctx* ctx, int cls, long long* launches, double* ms, dou
  * the first call on each device -- make that first call before any stream
  * capture.  Limits: rows * cols <= 1048576 and min(rows, cols) <= 4096, else
  * CTM_ERR_ARG.  All calls share the array: calls whose GPU work overlaps race
- * and must be serialised.  The call synchronises `stream` (a cudaStream_t) to
+ * and must be serialised.  Its cooperative Jacobi launch is ordered with every
+ * other cooperative launch of the library on the device (one internal stream
+ * per device, joined to `stream` with events), as a context's are.  The call synchronises `stream` (a cudaStream_t) to
  * report CTM_ERR_NOCONV / CTM_ERR_CUDA.  M is not modified.
  */
 int ctm_singular_values_noalloc(const double* M, int rows, int cols, double* s,
@@ -208,6 +210,9 @@ int ctm_singular_values_noalloc(const double* M, int rows, int cols, double* s,
  *   E_ij = s_j^2 - s_i^2, F_ii = 0 (Liao, Liu, Wang & Xiang 2019; the second
  *   term, Townsend 2016, vanishes when rows <= cols).
  * s and Vt receive no gradient (a projector v v^T uses the left vectors only).
+ * Rank-deficient or degenerate input gives a finite gM: with eps = 0 an exactly
+ * degenerate pair (s_i = s_j) gets F_ij = 0, and a zero singular value s_j
+ * (j < k) gets the pseudo-inverse 0 in diag(s_k)^-1.
  * Stream-ordered on `stream` (a cudaStream_t); temporaries come from the
  * stream-ordered pool; no synchronisation.  Inputs are not modified.
  * Errors: CTM_ERR_ARG (null pointer, k outside [1, r], eps < 0), CTM_ERR_OOM,
@@ -224,6 +229,21 @@ int ctm_svd_left_adjoint(const double* U, const double* s, const double* Vt, con
  */
 int ctm_contract_test(int precision, long long M, long long N, long long K, const double* A,
                       const double* B, double* C);
+
+/*
+ * Test hook for the projector factorisation (no counterpart in the paper; it
+ * exposes the truncated SVD that Sec. II-IV and Fig. 4a rely on): U (host,
+ * row-major rows x k) receives the leading k left singular vectors of the host
+ * row-major matrix M (rows x cols), 1 <= k <= min(rows, cols), computed in FP64
+ * on the current device.  path 0 = the library's own choice (exact one-sided
+ * Jacobi when min(rows, cols) <= 2048, else the randomized subspace iteration
+ * run to convergence), 1 = exact Jacobi, 2 = randomized subspace iteration.
+ * k = rows gives the identity.  Columns are sign-fixed (largest-magnitude entry
+ * positive) only on the exact path; compare spans, not columns.  Allocates its
+ * own device memory; synchronous.  Errors: CTM_ERR_ARG, CTM_ERR_OOM,
+ * CTM_ERR_CUDA, CTM_ERR_NOCONV.
+ */
+int ctm_truncated_svd_test(int path, const double* M, int rows, int cols, int k, double* U);
 
 /*
  * Batching of independent states (no counterpart in the paper: many iPEPS

@@ -23,7 +23,9 @@ where dU is the incoming gradient zero-padded to all columns and
 F_ij = 1 / (s_j^2 - s_i^2) off the diagonal, broadened to
 (s_j^2 - s_i^2) / ((s_j^2 - s_i^2)^2 + eps s_max^4) (Liao, Liu, Wang & Xiang,
 PRX 9, 031041 (2019), there with s_max = 1) so that degenerate pairs contribute
-zero instead of dividing by zero.  The broadening is relative to the largest
+zero instead of dividing by zero; with eps = 0 an exactly degenerate pair is
+given F_ij = 0 and a zero singular value the pseudo-inverse 0 in S^-1 (the
+eps -> 0+ limits of the broadened forms).  The broadening is relative to the largest
 singular value: the matrices of a CTM move carry no fixed scale.  The second
 term carries the part of dU outside the span of U (Townsend, "Differentiating
 the singular value decomposition", 2016).  S and V^T receive no
@@ -77,13 +79,22 @@ def svd_left_adjoint(U, S, Vh, gUk, eps):
     gU[:, :k] = gUk
     J = U.T @ gU
     E = S[None, :] ** 2 - S[:, None] ** 2          # E_ij = s_j^2 - s_i^2
-    F = E / (E * E + eps * S[0] ** 4)                # eps relative to s_max^4
+    den = E * E + eps * S[0] ** 4                    # eps relative to s_max^4
+    # a pair with den = 0 (exactly degenerate, no broadening) contributes zero:
+    # the eps -> 0+ limit of the broadened factor at E = 0
+    F = torch.where(den > 0, E / torch.where(den > 0, den, torch.ones_like(den)),
+                    torch.zeros_like(E))
     F.fill_diagonal_(0.0)
     inner = (F * (J - J.T)) * S[None, :]             # (F o skew) S
     gM = U @ inner @ Vh
     if m > r:  # part of dU outside span(U); only the kept columns are non-zero
         gperp = gU - U @ J
-        gM = gM + (gperp[:, :k] / S[None, :k]) @ Vh[:k, :]
+        # pseudo-inverse of S: a zero singular value contributes zero (the limit
+        # of the broadened inverse s / (s^2 + eps) at s = 0)
+        sk = S[:k]
+        inv = torch.where(sk > 0, 1.0 / torch.where(sk > 0, sk, torch.ones_like(sk)),
+                          torch.zeros_like(sk))
+        gM = gM + (gperp[:, :k] * inv[None, :]) @ Vh[:k, :]
     return gM
 
 

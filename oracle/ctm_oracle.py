@@ -26,8 +26,8 @@ Methods for PEPS"):
 Every SVD here is an exact LAPACK SVD (numpy.linalg.svd).  Nothing is blocked,
 fused or reordered beyond the contraction sequences the paper describes.
 
-Conventions (readings of the stripped figures; each is listed with its reason
-in the design notes):
+Conventions (the figures the labels refer to carry no printed leg order, so each
+of these is a reading, chosen to agree with every label the text uses):
 
 * Site tensors A[p, u, l, d, r].  Site (i, j) holds A when i + j is even.
 * Environment tensors are labelled (kind, k, x): k = 1 left, 2 top, 3 right,
@@ -491,6 +491,43 @@ def bond_rdm(env, A, B, r, x):
 
 
 BONDS = {0: (0, "a"), 1: (0, "b"), 2: (1, "a"), 3: (1, "b")}
+
+
+def bond_rdm_seq(env, A, B, r, x):
+    """The same density matrix as ``bond_rdm``, with each site's ket layer and bra
+    layer absorbed one after the other (the order of Sec. IV applied to the
+    observable) instead of through the open double-layer tensor: the largest
+    intermediate is chi^2 d^2 D^4 instead of chi^2 D^6, which makes the energy
+    computable at D = 6..8."""
+    y = OTHER[x]
+    V = View(env, r)
+    Sx, Sy = rotate_site({"a": A, "b": B}[x], r), rotate_site({"a": A, "b": B}[y], r)
+    d = A.shape[0]
+    # left half: frame (C1 T2 T1) with the ket and bra of x, closed by (T4 C4)
+    top = ein("dg,gKBe->dKBe", V("C", 1, x), V("T", 2, x))        # [down, Uk, Ub, e]
+    top = ein("dKBe,mLld->mLlKBe", top, V("T", 1, x))              # [m, Lk, Lb, Uk, Ub, e]
+    ket = ein("mLlKBe,pKLnr->mlBepnr", top, Sx)                     # ket: u = Uk, l = Lk
+    both = ein("mlBepnr,PBlNR->mepnrPNR", ket, Sx.conj())           # bra: u = Ub, l = Lb
+    bot = ein("jnNo,om->jnNm", V("T", 4, x), V("C", 4, x))          # T4 [right, k, b, left]
+    left = ein("mepnrPNR,jnNm->ejrRpP", both, bot)                  # [e, j, Rk, Rb, p, P]
+    # right half: frame (T2 C2 T3) with the ket and bra of y, closed by (C3 T4)
+    top = ein("eKBz,zh->eKBh", V("T", 2, y), V("C", 2, y))          # [e, Uk, Ub, h]
+    top = ein("eKBh,hWwt->eKBWwt", top, V("T", 3, y))               # [e, Uk, Ub, Rk, Rb, t]
+    ket = ein("eKBWwt,qKlnW->eBwtqln", top, Sy)                     # ket: u = Uk, r = Rk
+    both = ein("eBwtqln,QBLNw->etqlnQLN", ket, Sy.conj())           # bra: u = Ub, r = Rb
+    bot = ein("ti,inNj->tnNj", V("C", 3, y), V("T", 4, y))          # T4 [right, k, b, left]
+    right = ein("etqlnQLN,tnNj->ejlLqQ", both, bot)                 # [e, j, Lk, Lb, q, Q]
+    rho = ein("ejrRpP,ejrRqQ->pqPQ", left, right)
+    return rho.reshape(d * d, d * d)
+
+
+def expect_bond_seq(env, A, B, bond, op):
+    """``expect_bond`` through ``bond_rdm_seq`` (for D where the open double layer
+    does not fit)."""
+    r, x = BONDS[bond]
+    rho = bond_rdm_seq(env, A, B, r, x)
+    return float(np.trace(rho @ op) / np.trace(rho))
+
 
 
 def expect_bond(env, A, B, bond, op):

@@ -11,7 +11,9 @@
 // Liu, Wang & Xiang (PRX 9, 031041, 2019), relative to the largest singular
 // value.  The second term (Townsend 2016) carries the part of gU outside the
 // span of U; it vanishes when rows <= cols (U square).  S and Vt get no
-// gradient: a projector v v^T uses the left vectors only.
+// gradient: a projector v v^T uses the left vectors only.  Rank-deficient and
+// degenerate inputs stay finite: with eps = 0 an exactly degenerate pair gets
+// F_ij = 0, and a zero singular value the pseudo-inverse 0 in diag(s_k)^-1.
 //
 // Four FP64 leg-map GEMMs and two element-wise kernels; the GEMMs carry all the
 // O(rows r^2 + rows r cols) work.
@@ -44,7 +46,8 @@ __global__ void adjoint_core_kernel(const double* __restrict__ J, const double* 
     double v = 0.0;
     if (i != j) {
       const double E = s[j] * s[j] - s[i] * s[i];
-      const double F = E / (E * E + floor);
+      const double den = E * E + floor;
+      const double F = den > 0.0 ? E / den : 0.0;  // exactly degenerate, eps = 0: zero
       const double jij = j < k ? J[(long long)i * k + j] : 0.0;
       const double jji = i < k ? J[(long long)j * k + i] : 0.0;
       v = F * (jij - jji) * s[j];
@@ -53,7 +56,8 @@ __global__ void adjoint_core_kernel(const double* __restrict__ J, const double* 
   }
 }
 
-// T[row, j] += P[row, j] / s_j for j < k  (T: rows x r, P: rows x k).
+// T[row, j] += P[row, j] / s_j for j < k  (T: rows x r, P: rows x k); a zero
+// singular value takes the pseudo-inverse 0.
 __global__ void add_scaled_kernel(double* __restrict__ T, const double* __restrict__ P,
                                   const double* __restrict__ s, int rows, int r, int k) {
   const long long n = (long long)rows * k;
@@ -61,7 +65,8 @@ __global__ void add_scaled_kernel(double* __restrict__ T, const double* __restri
        e += (long long)gridDim.x * blockDim.x) {
     const long long row = e / k;
     const int j = (int)(e - row * k);
-    T[row * r + j] += P[e] / s[j];
+    const double sj = s[j];
+    if (sj > 0.0) T[row * r + j] += P[e] / sj;
   }
 }
 

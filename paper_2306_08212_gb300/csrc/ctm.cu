@@ -32,10 +32,12 @@ void ck(cudaError_t e, const char* what) {
   if (e != cudaSuccess) fail(CTM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-constexpr int kExactSvdMax = 1024;  // exact one-sided Jacobi up to this size
+constexpr int kExactSvdMax = 2048;  // exact one-sided Jacobi up to this size
 constexpr int kFastMinSide = 0;  // mixed precision: subspace iteration for every size
-constexpr int kOversample = 16;    // randomized range finder: extra columns
-constexpr int kPowerIters = 2;     // randomized range finder: subspace iterations
+constexpr int kMinOversample = 16;  // randomized range finder: extra columns (at least)
+constexpr int kMaxPowerIters = 40;  // randomized range finder: subspace iteration cap
+constexpr int kCapturedPowerIters = 4;  // inside a stream capture (no host check possible)
+constexpr double kSubspaceTol = 1e-12;  // RMS sine of the principal angles between sweeps
 constexpr int kMaxSweeps = 60;
 
 }  // namespace
@@ -404,7 +406,7 @@ Tmp ein(ctm_ctx* c, const char* spec, const Ten& A, const Ten& B) {
   Tmp C(c, p.out_dims, p.out_nd);
   ProfScope ps(c, c->precision == CTM_TF32 ? 1 : 2, 2.0 * p.M * p.N * p.K, true);
   int rc = tc_contract(c->tc, c->stream, c->precision, p.M, p.N, p.K, A.p, p.Am, p.Ak, B.p,
-                       p.Bk, p.Bn, C.t.p, p.Cm, p.Cn, &c->launches, &c->flags->error, ps.ev0(),
+                       p.Bk, p.Bn, C.t.p, p.Cm, p.Cn, &c->launches, &c->flags->tc_timeout, ps.ev0(),
                        ps.ev1());
   if (rc != 0)
     fail(CTM_ERR_CUDA, std::string("tensor-core contraction failed (") + std::to_string(rc) + ", " +
@@ -445,8 +447,11 @@ Tmp sorted_unit_columns(ctm_ctx* c, double* X, int nrows, int ncols, int k) {
 // Leading k left singular vectors of the row-major matrix M (rows x cols):
 // U (row-major rows x k).  Exact one-sided Jacobi when the smaller side is at
 // most kExactSvdMax, else a randomized subspace iteration (Halko, Martinsson &
-// Tropp, SIAM Rev. 53, 217 (2011)) with a Jacobi SVD of the projected problem.
-Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k);
+// Tropp, SIAM Rev. 53, 217 (2011)) run until its leading-k subspace stops
+// moving, with a Jacobi SVD of the projected problem.  path: 0 = that choice,
+// 1 = exact, 2 = randomized (test hook).
+enum SvdPath { kSvdAuto = 0, kSvdExact = 1, kSvdRandomized = 2 };
+Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k, int path = kSvdAuto);
 
 
 // CTM_TRACE=1 prints every factorisation (shape, path, time, Jacobi sweeps of
@@ -482,10 +487,17 @@ Tmp left_svd(ctm_ctx* c, const double* M, int rows, int cols, int k) {
   return U;
 }
 
-Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k) {
+// Root-mean-square sine of the principal angles between the spans of the
+// leading k columns of Uold and Unew (row-major rows x ld, orthonormal columns):
+// ||Unew_k - Uold_k (Uold_k^T Unew_k)||_F / sqrt(k).  Synchronises the stream.
+double subspace_change(ctm_ctx* c, const double* Uold, const double* Unew, int rows, int ld,
+                       int k);
+
+Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k, int path) {
   if (k >= rows) return identity(c, rows);
   if (k > std::min(rows, cols)) fail(CTM_ERR_ARG, "truncation rank exceeds the matrix rank bound");
-  if (std::min(rows, cols) <= kExactSvdMax) {
+  const bool exact = path == kSvdExact || (path == kSvdAuto && std::min(rows, cols) <= kExactSvdMax);
+  if (exact) {
     if (cols <= rows) {
       // X = M column-major (transpose copy), Jacobi on its cols columns
       Tmp X(c, {cols, rows});
@@ -513,7 +525,7 @@ Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k) {
     dfree(c, perm);
     return U;
   }
-  const int l = std::min(k + kOversample, std::min(rows, cols));
+  const int l = std::min(k + std::max(kMinOversample, k / 2), std::min(rows, cols));
   LegMap Mrow, Mcol;
   // M(i, j) at i*cols + j
   push(Mrow, rows, cols);
@@ -560,7 +572,14 @@ Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k) {
   jacobi(c, Y.t.p, rows, l, nullptr);
   Tmp Q = sorted_unit_columns(c, Y.t.p, rows, l, l);
   Y.release();
-  for (int it = 0; it < kPowerIters; ++it) {
+  // Subspace iteration Q <- orth(M orth(M^T Q)).  After each sweep the columns
+  // of Q, sorted by norm before normalisation, are the left singular vectors of
+  // M orth(M^T Q); the sweeps stop when the span of their leading k no longer
+  // moves (kSubspaceTol), or after kMaxPowerIters.  Inside a stream capture the
+  // host cannot look, so a fixed count runs.
+  const int max_iters = c->capturing ? kCapturedPowerIters : kMaxPowerIters;
+  double prev_moved = INFINITY;
+  for (int it = 0; it < max_iters; ++it) {
     Tmp Z = times_Mt(Q.t.p);
     jacobi(c, Z.t.p, cols, l, nullptr);
     Tmp Qz = sorted_unit_columns(c, Z.t.p, cols, l, l);
@@ -568,7 +587,17 @@ Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k) {
     Tmp Y2 = times_M(Qz.t.p);
     Qz.release();
     jacobi(c, Y2.t.p, rows, l, nullptr);
-    Q = sorted_unit_columns(c, Y2.t.p, rows, l, l);
+    Tmp Qn = sorted_unit_columns(c, Y2.t.p, rows, l, l);
+    Y2.release();
+    const bool check = !c->capturing;
+    const double moved = check ? subspace_change(c, Q.t.p, Qn.t.p, rows, l, k) : 1.0;
+    Q = std::move(Qn);
+    if (trace_on() && check)
+      std::fprintf(stderr, "[ctm] range finder %dx%d k=%d l=%d sweep %d: subspace moved %.3e\n",
+                   rows, cols, k, l, it + 1, moved);
+    // converged, or down at the rounding floor (no longer shrinking)
+    if (moved < kSubspaceTol || (moved < 1e-10 && moved > 0.9 * prev_moved)) break;
+    prev_moved = moved;
   }
   // Rayleigh-Ritz: Z = M^T Q = (Q^T M)^T; Jacobi with V gives Q^T M = V S W^T
   Tmp Z = times_Mt(Q.t.p);
@@ -583,6 +612,50 @@ Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k) {
   dfree(c, perm);
   Ten Qv = view(Q.t, {rows, l});
   return ein64(c, "ic,cr->ir", Qv, Vk.t);
+}
+
+double subspace_change(ctm_ctx* c, const double* Uold, const double* Unew, int rows, int ld,
+                       int k) {
+  // S = Uold_k^T Unew_k (k x k)
+  Tmp S(c, {k, k});
+  {
+    LegMap Am, Ak, Bk, Bn, Cm, Cn;
+    push(Am, k, 1);
+    push(Ak, rows, ld);
+    push(Bk, rows, ld);
+    push(Bn, k, 1);
+    push(Cm, k, k);
+    push(Cn, k, 1);
+    ProfScope ps(c, 0, 2.0 * k * k * rows);
+    ck(gemm_f64(c->stream, k, k, rows, 1.0, Uold, Am, Ak, Unew, Bk, Bn, 0.0, S.t.p, Cm, Cn),
+       "U^T U");
+    ++c->launches;
+  }
+  // R = Unew_k - Uold_k S
+  Tmp R(c, {rows, k});
+  {
+    LegMap m;
+    push(m, rows, ld);
+    push(m, k, 1);
+    ck(permute_f64(c->stream, R.t.p, Unew, m), "copy");
+    ++c->launches;
+    LegMap Am, Ak, Bk, Bn, Cm, Cn;
+    push(Am, rows, ld);
+    push(Ak, k, 1);
+    push(Bk, k, k);
+    push(Bn, k, 1);
+    push(Cm, rows, k);
+    push(Cn, k, 1);
+    ProfScope ps(c, 0, 2.0 * k * k * rows);
+    ck(gemm_f64(c->stream, rows, k, k, -1.0, Uold, Am, Ak, S.t.p, Bk, Bn, 1.0, R.t.p, Cm, Cn),
+       "R");
+    ++c->launches;
+  }
+  Tmp nn = ein64(c, "ij,ij->", R.t, R.t);
+  double v = 0.0;
+  ck(cudaMemcpyAsync(&v, nn.t.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "d2h");
+  ck(cudaStreamSynchronize(c->stream), "sync");
+  return std::sqrt(std::max(v, 0.0) / k);
 }
 
 // ---------------------------------------------------------------------------
@@ -612,7 +685,7 @@ void gemm_mixed(ctm_ctx* c, long long M, long long N, long long K, const double*
   }
   ProfScope ps(c, c->precision == CTM_TF32 ? 1 : 2, 2.0 * M * N * K, true);
   if (tc_contract(c->tc, c->stream, c->precision, M, N, K, A, Am, Ak, B, Bk, Bn, C, Cm, Cn,
-                  &c->launches, &c->flags->error, ps.ev0(), ps.ev1()) != 0)
+                  &c->launches, &c->flags->tc_timeout, ps.ev0(), ps.ev1()) != 0)
     fail(CTM_ERR_CUDA, "tensor-core sketch product failed");
 }
 
@@ -1048,9 +1121,10 @@ void check_flags(ctm_ctx* c) {
   DevFlags h;
   ck(cudaMemcpyAsync(&h, c->flags, sizeof(DevFlags), cudaMemcpyDeviceToHost, c->stream), "flags");
   ck(cudaStreamSynchronize(c->stream), "sync");
-  if (h.error || h.noconv || h.bad) {
+  if (h.error || h.noconv || h.bad || h.tc_timeout) {
     ck(cudaMemsetAsync(c->flags, 0, sizeof(DevFlags), c->stream), "flags reset");
     if (h.error) fail(CTM_ERR_CUDA, "a grid barrier timed out");
+    if (h.tc_timeout) fail(CTM_ERR_CUDA, "a tensor-core pipeline wait timed out");
     if (h.bad) fail(CTM_ERR_NAN, "a new environment tensor was zero or not finite");
     fail(CTM_ERR_NOCONV, "a Jacobi SVD reached its sweep cap");
   }
@@ -1947,6 +2021,33 @@ int ctm_contract_test(int precision, long long M, long long N, long long K, cons
   cudaFree(dB);
   cudaFree(dC);
   tc_destroy(tc);
+  return rc;
+}
+
+int ctm_truncated_svd_test(int path, const double* M, int rows, int cols, int k, double* U) {
+  if (!M || !U || rows < 1 || cols < 1 || k < 1 || k > std::min(rows, cols) || path < 0 ||
+      path > 2)
+    return CTM_ERR_ARG;
+  ctm_ctx* c = new (std::nothrow) ctm_ctx;
+  if (!c) return CTM_ERR_OOM;
+  int rc = guarded(c, [&] {
+    void* f = nullptr;
+    ck(cudaMalloc(&f, sizeof(DevFlags)), "flags");
+    c->owned.push_back(f);
+    c->flags = (DevFlags*)f;
+    ck(cudaMemset(c->flags, 0, sizeof(DevFlags)), "flags");
+    if (!coop_stream()) fail(CTM_ERR_CUDA, "cooperative stream");
+    double* dM = owned_alloc(c, (long long)rows * cols);
+    ck(cudaMemcpy(dM, M, sizeof(double) * (size_t)rows * cols, cudaMemcpyHostToDevice), "h2d");
+    Tmp Uk = left_svd_impl(c, dM, rows, cols, k, path);
+    if (Uk.t.size() != (long long)rows * k) fail(CTM_ERR_ARG, "internal: factor shape");
+    ck(cudaMemcpyAsync(U, Uk.t.p, sizeof(double) * (size_t)rows * k, cudaMemcpyDeviceToHost,
+                       c->stream),
+       "d2h");
+    Uk.release();
+    check_flags(c);
+  });
+  ctm_free(c);
   return rc;
 }
 

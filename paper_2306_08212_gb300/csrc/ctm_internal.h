@@ -62,6 +62,8 @@ struct DevFlags {
   int noconv;                     // sticky: a Jacobi sweep cap was reached
   int bad;                        // sticky: a normalised tensor was zero or not finite
   int sweeps;                     // sweeps used by the last Jacobi launch
+  int tc_timeout;                 // sticky: a tensor-core pipeline wait timed out (written
+                                  // by those kernels only, never read by a kernel)
 };
 constexpr size_t kDevFlagsResetBytes = 32;  // offsetof(DevFlags, error)
 

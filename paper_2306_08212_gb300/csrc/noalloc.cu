@@ -19,7 +19,11 @@
 // All calls share the one array and it keeps the last call's contents: each
 // call clears the words that must start at zero.  Calls whose GPU work overlaps
 // (different streams, or different host threads on one device) race on the
-// array and give wrong results; serialise them.
+// array and give wrong results; serialise them.  The Jacobi sweep itself is a
+// cooperative launch issued, like every cooperative launch of this library, on
+// one internal stream per device (created at the first such launch), ordered
+// after the caller's stream with events; so it never waits on SMs held by a
+// context's own cooperative kernels.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -119,7 +123,11 @@ extern "C" int ctm_singular_values_noalloc(const double* M, int rows, int cols, 
       return CTM_ERR_CUDA;
   }
   long long launches = 0;
-  if (jacobi_batched(st, X, nrows, ncols, 1, 0, flags, 60, &launches, kValuesOnlyTol, false) != 0)
+  // serialize = true: the cooperative launch runs on the library's one
+  // cooperative stream of this device, ordered after the work already issued on
+  // `stream`, so it never contends with a context's own Jacobi launches for
+  // co-residency (events only; no device memory is allocated)
+  if (jacobi_batched(st, X, nrows, ncols, 1, 0, flags, 60, &launches, kValuesOnlyTol, true) != 0)
     return CTM_ERR_CUDA;
   if (column_norms_sorted(st, X, nrows, ncols, sig, perm) != cudaSuccess) return CTM_ERR_CUDA;
   sorted_unit_values_kernel<<<1, 256, 0, st>>>(sig, perm, ncols, s);

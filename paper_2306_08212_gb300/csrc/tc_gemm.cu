@@ -6,8 +6,11 @@
 // the result through the output leg map.
 //
 // Every wait on an mbarrier has a time limit (about one second of
-// %globaltimer); on expiry the kernel records an error word, skips the rest of
-// its work, releases its TMEM and returns.
+// %globaltimer); on expiry the kernel records an error word and stops issuing
+// work, then waits (again with a limit) until every TMA copy it issued has
+// landed and every MMA it issued has completed, releases its TMEM and returns.
+// The error word is only written by the kernel, never read: a timeout elsewhere
+// (another kernel, another launch) cannot make a launch abandon its own copies.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -67,16 +70,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 
 constexpr uint64_t kWaitLimitNs = 1000000000ull;  // one second
 
-// Bounded wait on an mbarrier phase; false on timeout or when another thread
-// already reported an error.
+// Bounded wait on an mbarrier phase; false (and the error word set) on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = globaltimer_ns();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (*(volatile int*)err) return false;
     if (globaltimer_ns() - t0 > kWaitLimitNs) {
-      atomicExch(err, 1);
+      if (err) atomicExch(err, 1);
       return false;
     }
   }
@@ -222,9 +223,13 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
+  // Number of k-tiles whose TMA loads were issued (producer) and whose MMAs
+  // were issued (MMA thread); equal to num_k_tiles unless a wait timed out.
+  __shared__ int s_issued, s_consumed;
   if (warp == 0 && lane == 0) {
     // producer: TMA
-    for (int kt = 0; kt < num_k_tiles; ++kt) {
+    int kt = 0;
+    for (; kt < num_k_tiles; ++kt) {
       const int s = kt % STAGES;
       const uint32_t it = kt / STAGES;
       if (!mbar_wait(&empty[s], (it & 1u) ^ 1u, err)) break;
@@ -232,9 +237,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       tma_load_2d(sA + s * A_BYTES, &mapA, &full[s], kt * KE, m0);
       tma_load_2d(sB + s * B_BYTES, &mapB, &full[s], kt * KE, n0);
     }
+    s_issued = kt;
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    for (int kt = 0; kt < num_k_tiles; ++kt) {
+    int kt = 0;
+    for (; kt < num_k_tiles; ++kt) {
       const int s = kt % STAGES;
       const uint32_t it = kt / STAGES;
       if (!mbar_wait(&full[s], it & 1u, err)) break;
@@ -246,6 +253,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         umma<TF32>(tmem, adesc + 2ull * k, bdesc + 2ull * k, IDESC, (kt | k) != 0);
       umma_commit(&empty[s]);
     }
+    s_consumed = kt;
+    // arrives once every MMA issued above has completed (also after a timeout)
     umma_commit(done);
   }
   __syncwarp();
@@ -270,6 +279,14 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     }
   }
   tc_fence_before();
+  __syncthreads();
+  // After a timeout: TMA loads issued for k-tiles the MMA thread never reached
+  // may still be writing this CTA's shared memory.  Wait (bounded) for each of
+  // them to land before the CTA releases its resources.
+  if (threadIdx.x == 0 && s_consumed < s_issued) {
+    for (int kt = s_consumed; kt < s_issued; ++kt)
+      mbar_wait(&full[kt % STAGES], (uint32_t)(kt / STAGES) & 1u, err);
+  }
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),

@@ -50,6 +50,8 @@ SIGNATURES = {
                                              ctypes.c_int, ctypes.c_double, _P, _P]),
     "ctm_contract_test": (ctypes.c_int, [ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong,
                                           ctypes.c_longlong, _D, _D, _D]),
+    "ctm_truncated_svd_test": (ctypes.c_int, [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int,
+                                               ctypes.c_int, _D]),
     "ctm_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int]),
     "ctm_batch_move": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "ctm_batch_last_error": (ctypes.c_char_p, [_P]),
@@ -237,6 +239,16 @@ def ctm_singular_values_noalloc(M_ptr, rows, cols, s_ptr, stream=None):
     st = stream if stream is not None else _current_stream()
     return load().ctm_singular_values_noalloc(ctypes.c_void_p(M_ptr), int(rows), int(cols),
                                               ctypes.c_void_p(s_ptr), st)
+
+
+def ctm_truncated_svd_test(path, M, k):
+    """Leading k left singular vectors of the host matrix M in FP64 on the GPU
+    (path 0 = library choice, 1 = exact Jacobi, 2 = randomized).  Returns (status, U)."""
+    M = np.ascontiguousarray(M, dtype=np.float64)
+    rows, cols = M.shape
+    U = np.zeros((rows, int(k)))
+    rc = load().ctm_truncated_svd_test(int(path), _dptr(M), rows, cols, int(k), _dptr(U))
+    return rc, U
 
 
 def ctm_svd_left_adjoint(U, s, Vt, gU, eps=1e-12, stream=None):

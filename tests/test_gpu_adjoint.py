@@ -58,3 +58,20 @@ def test_bad_arguments(ctm):
     assert rc == ctm.ERR_ARG
     rc, _ = ctm.ctm_svd_left_adjoint(U, s, Vt, np.zeros((6, 2)), -1.0)  # eps < 0
     assert rc == ctm.ERR_ARG
+
+
+@pytest.mark.parametrize("eps", [0.0, 1e-12])
+def test_rank_deficient_tall_matrix(ctm, eps):
+    """A tall 40 x 12 matrix of rank 7 with k = 10 kept columns: three kept
+    singular values are zero (and exactly degenerate with each other).  Both
+    sides take the pseudo-inverse convention; the result is finite and equal."""
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((40, 7)) @ rng.standard_normal((7, 12))
+    U, s, Vt = np.linalg.svd(X, full_matrices=False)
+    s[7:] = 0.0  # exact zeros (LAPACK returns ~1e-15 there)
+    _check(ctm, U, s, Vt, rng.standard_normal((40, 10)), eps)
+
+
+def test_zero_matrix(ctm):
+    """s = 0 everywhere: every term takes the zero convention, gM = 0."""
+    _check(ctm, np.eye(5)[:, :3], np.zeros(3), np.eye(3), np.ones((5, 2)), 0.0)

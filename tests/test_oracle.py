@@ -95,6 +95,8 @@ def test_fold_and_exact_moves_match_brute_force(mode):
         ref = brute.finite_rdm(A, B, 3, 8, ((1, 3), (1, 4)), a_parity=par)
         rho = O.bond_rdm(env, A, B, 0, "a" if bond == 0 else "b")
         np.testing.assert_allclose(rho / np.trace(rho), ref / np.trace(ref), atol=1e-12)
+        rho = O.bond_rdm_seq(env, A, B, 0, "a" if bond == 0 else "b")
+        np.testing.assert_allclose(rho / np.trace(rho), ref / np.trace(ref), atol=1e-12)
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -110,6 +112,8 @@ def test_exact_vertical_moves_match_brute_force(mode):
     for x, par in (("a", 0), ("b", 1)):
         ref = brute.finite_rdm(Ar, Br, 3, 8, ((1, 3), (1, 4)), a_parity=par)
         rho = O.bond_rdm(env, A, B, 1, x)
+        np.testing.assert_allclose(rho / np.trace(rho), ref / np.trace(ref), atol=1e-12)
+        rho = O.bond_rdm_seq(env, A, B, 1, x)
         np.testing.assert_allclose(rho / np.trace(rho), ref / np.trace(ref), atol=1e-12)
 
 
@@ -136,6 +140,50 @@ def test_neel_product_state_energy():
     O.converge(env, A, B, 4, 4, "reduced_sequential", max_iter=2)
     for bond in range(4):
         assert abs(O.expect_bond(env, A, B, bond, O.heisenberg_bond()) + 0.25) < 1e-15
+
+
+@pytest.mark.parametrize("D,chi,seed", [(2, 6, 1), (3, 5, 2)])
+def test_sequential_bond_rdm_equals_double_layer(D, chi, seed):
+    """bond_rdm_seq (ket and bra layers in turn) and bond_rdm (open double layer) are
+    the same contraction in two orders: equal on random environments for all four
+    bonds, and a planted swap of a site's ket legs breaks the equality."""
+    A, B = I.random_sites(2, D, seed)
+    env = I.random_env_tensors(D, chi, seed=seed + 10)
+    for bond in range(4):
+        r, x = O.BONDS[bond]
+        a, b = O.bond_rdm(env, A, B, r, x), O.bond_rdm_seq(env, A, B, r, x)
+        np.testing.assert_allclose(b, a, rtol=0, atol=1e-13 * np.abs(a).max())
+    Bbad = B.transpose(0, 2, 1, 3, 4)  # u and l exchanged on one site
+    a = O.bond_rdm(env, A, Bbad, 0, "a")
+    b = O.bond_rdm_seq(env, A, B, 0, "a")
+    assert np.abs(a / np.trace(a) - b / np.trace(b)).max() > 1e-3
+
+
+def test_heisenberg_bond_is_the_spin_half_exchange():
+    """Pins the operator of Eq. 1 as read here (S = sigma/2, antiferromagnetic sign),
+    including its Sy Sy term, which the real product and Neel states cannot see:
+    * for two spins 1/2, S_i . S_j = P/2 - 1/4 with P the swap of the two sites;
+    * its spectrum is {-3/4 (singlet), 1/4, 1/4, 1/4 (triplet)};
+    * the singlet (|01> - |10>)/sqrt 2 has -3/4, and (|00> + |11>)/sqrt 2 and
+      (|00> - |11>)/sqrt 2, whose energies differ in sign if Sy Sy does, both 1/4;
+    * the Sy Sy part equals kron(sy, sy) built from the complex Pauli matrix."""
+    H = O.heisenberg_bond()
+    swap = np.zeros((4, 4))
+    for i in range(2):
+        for j in range(2):
+            swap[2 * j + i, 2 * i + j] = 1.0
+    np.testing.assert_allclose(H, swap / 2 - np.eye(4) / 4, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(np.linalg.eigvalsh(H), [-0.75, 0.25, 0.25, 0.25], rtol=0, atol=1e-15)
+    singlet = np.array([0, 1, -1, 0]) / np.sqrt(2)
+    np.testing.assert_allclose(H @ singlet, -0.75 * singlet, rtol=0, atol=1e-15)
+    for v in (np.array([1, 0, 0, 1]) / np.sqrt(2), np.array([1, 0, 0, -1]) / np.sqrt(2)):
+        np.testing.assert_allclose(H @ v, 0.25 * v, rtol=0, atol=1e-15)
+    sy = np.array([[0, -1j], [1j, 0]]) / 2
+    sx = np.array([[0, 1], [1, 0]]) / 2
+    sz = np.diag([0.5, -0.5])
+    yy = H - np.kron(sx, sx) - np.kron(sz, sz)
+    np.testing.assert_allclose(yy, np.kron(sy, sy).real, rtol=0, atol=1e-15)
+    assert np.abs(np.kron(sy, sy).imag).max() == 0.0
 
 
 def test_onsager_closed_forms_agree_with_each_other():

@@ -109,6 +109,38 @@ def test_degenerate_kept_singular_values():
     np.testing.assert_allclose(g, fd, rtol=0, atol=1e-6 * np.abs(fd).max())
 
 
+def test_rank_deficient_kept_columns_pseudo_inverse():
+    """M of rank 7 (40 x 12), k = 10 kept columns, three of them with s = 0.  A loss
+    that depends only on the seven columns with s > 0 (sign-invariant: sum of
+    c_ij u_ij^2) has a well-defined gradient; the adjoint with the zero conventions
+    (F_ij = 0 for the degenerate zero pair, pseudo-inverse 0 for s = 0) equals its
+    central differences, where a plain 1/s or 1/(s_j^2 - s_i^2) gives NaN."""
+    rng = np.random.default_rng(5)
+    M0 = rng.standard_normal((40, 7)) @ rng.standard_normal((7, 12))
+    c = rng.standard_normal((40, 7))
+
+    def loss(M):
+        U = np.linalg.svd(M, full_matrices=False)[0]
+        return float(np.sum(c * U[:, :7] ** 2))
+
+    U, s, Vt = np.linalg.svd(M0, full_matrices=False)
+    s[7:] = 0.0
+    gU = np.zeros((40, 10))
+    gU[:, :7] = 2 * c * U[:, :7]
+    for eps in (0.0, 1e-12):
+        g = G.svd_left_adjoint(*(torch.tensor(x) for x in (U, s, Vt, gU)), eps).numpy()
+        assert np.all(np.isfinite(g))
+        if eps == 0.0:
+            h = 1e-6
+            fd = np.zeros_like(M0)
+            for idx in np.ndindex(M0.shape):
+                Mp, Mm = M0.copy(), M0.copy()
+                Mp[idx] += h
+                Mm[idx] -= h
+                fd[idx] = (loss(Mp) - loss(Mm)) / (2 * h)
+            np.testing.assert_allclose(g, fd, rtol=0, atol=1e-6 * np.abs(fd).max())
+
+
 def test_energy_gradient_matches_central_differences():
     """D=2, chi=6: all 32 entries of A and all 32 of B (64 in total), one iteration."""
     A, B, env0 = _setup()
