@@ -212,15 +212,20 @@ def _run_native(args):
 
     for _ in range(args.warmup):
         step()
-    # untimed profiling steps with every kernel class timed (CUDA events, also
-    # as event nodes of the recaptured graphs): the per-class breakdown of one
-    # steady-state step, and the class with the most device time among the
-    # contractions
-    ctm.ctm_kernel_stats_reset(ctx, 0xF)
+    # untimed calibration step: every kernel class timed with CUDA events while
+    # the context runs on its own stream alone (no side streams, no graphs), so
+    # no two of its kernels overlap and each class's summed event time is its
+    # own device time; also picks the contraction class with the most device time
+    ctm.ctm_kernel_stats_reset(ctx, 0x1F | ctm.PROFILE_SERIAL)
     step()
+    ctm.ctm_kernel_stats_reset(ctx, 0x1F | ctm.PROFILE_SERIAL)  # counters cleared
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
     step()
-    ctm.ctm_kernel_stats_reset(ctx, 0xF)  # same mask: counters cleared, graphs kept
-    step()
+    c1.record(stream)
+    torch.cuda.synchronize()
+    calib_ms = c0.elapsed_time(c1)
     breakdown = ctm.ctm_kernel_stats(ctx)
     gemm_like = [k for k in breakdown if k["flops"] > 0]
     top = max(gemm_like, key=lambda k: k["ms"]) if gemm_like else None
@@ -277,7 +282,7 @@ def _run_native(args):
 
     std = None
     if not args.no_standard and rank == 0:
-        std = time_standard(args, A, B, host_env)
+        std = standard_vs_reduced(args, A, B, host_env)
 
     if rank != 0:
         env.free()
@@ -306,37 +311,77 @@ def _run_native(args):
         "kernel_classes": {k["name"]: {"launches": k["count"], "ms_per_step": k["ms"],
                                        "gflop_per_step": k["flops"] / 1e9}
                            for k in breakdown},
+        "kernel_classes_method": ("one untimed calibration step on a single stream, eager "
+                                  "(no side streams, no graphs): CUDA events around every "
+                                  "launch of a class, summed"),
+        "calibration_ms_per_step": calib_ms,
         "clocks": clk,
         "roofline": roof,
         "tensor_cores": tensor_core_util(breakdown, 1e3 * t / args.steps, peaks),
     }
     if std is not None:
-        line["fp64_standard"] = std
-        line["speedup_vs_fp64_standard"] = value / std["value"]
+        line["fp64_standard"] = std["fp64_standard"]
+        line["equal_accuracy"] = std["equal_accuracy"]
+        line["speedup_vs_fp64_standard"] = value / std["fp64_standard"]["value"]
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args)
     env.free()
     return line
 
 
-def time_standard(args, A, B, host_env):
-    """One FP64 standard move (Sec. II, O(chi^3 D^6)) on the same environment."""
+def standard_vs_reduced(args, A, B, host_env, moves=("left", "up", "right")):
+    """The FP64 standard move (Sec. II, O(chi^3 D^6)) beside the reduced-sequential move,
+    both from the same environment (the bench context's after its timed steps): the
+    standard rate from the 2nd and 3rd moves (the 1st is a warm-up), and the mean bond
+    energy (Heisenberg S.S) after the same three moves in FP64 standard, FP64
+    reduced-sequential and the bench's precision."""
+    import numpy as np
     import torch
 
     from paper_2306_08212_gb300 import ctm
-    env = ctm.Env(A, B, args.chi, precision=ctm.FP64 | ctm.INIT_NO_GROW)
-    for (kind, k, x), v in host_env.items():
-        env.set_tensor(kind, k, x, v.numpy())
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    env.move("left", "standard")
-    e1.record()
-    torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / 1e3
-    env.free()
-    return {"value": 1.0 / t, "unit": "moves/s", "moves_timed": 1, "dtype": "f64"}
+    sx = np.array([[0, 1], [1, 0]]) / 2
+    sz = np.diag([0.5, -0.5])
+    sy_sy = np.kron(np.array([[0, -1], [1, 0]]), np.array([[0, -1], [1, 0]])) / -4
+    H = np.kron(sx, sx) + sy_sy + np.kron(sz, sz)
+
+    def run(prec, mode):
+        env = ctm.Env(A, B, args.chi, precision=ctm.PRECISIONS[prec] | ctm.INIT_NO_GROW)
+        try:
+            for (kind, k, x), v in host_env.items():
+                env.set_tensor(kind, k, x, v.numpy())
+            times = []
+            for d in moves:
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                env.move(d, mode)
+                e1.record()
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1) / 1e3)
+            energy = float(np.mean([env.expect_bond(b, H) for b in range(4)]))
+            return times, energy
+        finally:
+            env.free()
+
+    t_std, e_std = run("fp64", "standard")
+    t_seq64, e_seq64 = run("fp64", "reduced_sequential")
+    _, e_seq = run(args.precision, "reduced_sequential")
+    timed = t_std[1:]
+    return {
+        "fp64_standard": {"value": len(timed) / sum(timed), "unit": "moves/s",
+                          "moves_timed": len(timed), "warmup_moves": 1,
+                          "seconds_per_move": timed, "dtype": "f64"},
+        "equal_accuracy": {
+            "start": "the bench context's environment after its timed steps",
+            "moves": list(moves), "observable": "mean Heisenberg S.S over the 4 bonds",
+            "energy_fp64_standard": e_std, "energy_fp64_reduced_sequential": e_seq64,
+            f"energy_{args.precision}_reduced_sequential": e_seq,
+            "dE_vs_standard": e_seq - e_std,
+            "dE_method_fp64": e_seq64 - e_std,
+            "dE_precision": e_seq - e_seq64,
+            "fp64_reduced_sequential_seconds_per_move": t_seq64},
+    }
 
 
 def tensor_core_util(breakdown, ms_per_step, peaks):
@@ -355,11 +400,26 @@ def tensor_core_util(breakdown, ms_per_step, peaks):
     return out
 
 
-# DRAM bytes (read + write) per launch from one ncu capture of each class on this workload
-# (profiles/gemm_f64_d8_chi256_bf16_step.md: mean of three 16x16-tile launches;
-# profiles/tc_gemm_d8_chi256_bf16_step.md: mean of three BN=256 launches).  Stale, and to be
-# set to None, as soon as the kernel changes.
-TRAFFIC_PER_LAUNCH = {"gemm_f64": 1.843e6, "tc_bf16_gemm": 9.25e6}
+# DRAM bytes (read + write) per launch of a kernel class, from one ncu capture of this
+# workload, valid only for the kernel source it was taken on: each entry names the source
+# file and the first 16 hex digits of its SHA-256 at capture time; when the file has changed
+# since, the bench reports traffic null.
+TRAFFIC_PER_LAUNCH = {}
+
+
+def measured_traffic(name):
+    import hashlib
+    entry = TRAFFIC_PER_LAUNCH.get(name)
+    if entry is None:
+        return None
+    src, sha, nbytes = entry
+    try:
+        with open(os.path.join(ROOT, src), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest()[:16] != sha:
+                return None
+    except OSError:
+        return None
+    return nbytes
 
 
 def roofline(args, stats, peaks, peaks_kind):
@@ -380,7 +440,7 @@ def roofline(args, stats, peaks, peaks_kind):
         peak, bound, note = fp64_gemm_peak(), "alu", "fp64: cuBLAS DGEMM measured here"
     return {"kernel": top["name"], "bound": bound, "achieved": achieved, "peak": peak,
             "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": (TRAFFIC_PER_LAUNCH.get(top["name"])
+            "traffic": (measured_traffic(top["name"])
                         if (args.D, args.chi, args.precision) == (D_, CHI, "bf16") else None),
             "launches": top["count"], "avg_launch_us": avg_s * 1e6, "peak_source": note}
 

@@ -161,7 +161,8 @@ long long ctm_kernel_launches(ctm_ctx* ctx);
  * Per-class kernel timing (measurement; no counterpart in the paper) with CUDA
  * events recorded on the context's stream around every launch of a class
  * (0 = FP64 contraction, 1 = TF32 tensor-core contraction, 2 = BF16 tensor-core
- * contraction, 3 = Jacobi SVD sweep kernel).
+ * contraction, 3 = Jacobi SVD sweep kernel, 4 = fused FP64 CholeskyQR, whose
+ * flop count is passes x (2 rows n^2 + n^3 / 3)).
  * ctm_profile_enable(ctx, mask) clears the counters and records the classes
  * whose bit (1 << class) is set in mask; 0 stops.  Changing the mask discards
  * the context's recorded CUDA graphs (they are recaptured with event nodes for
@@ -171,7 +172,12 @@ long long ctm_kernel_launches(ctm_ctx* ctx);
  * count (2 M N K for a contraction, 0 for Jacobi whose work depends on the
  * data).  When the FP64 class is the only one timed (mask 1), one of its
  * launches in eight is timed.
+ * With CTM_PROFILE_SERIAL OR-ed into the mask, moves run eagerly on the
+ * context's stream alone (no side streams, no CUDA graphs) until the mask is
+ * changed: a calibration mode in which no two kernels of the context overlap, so
+ * each class's summed event time is its own device time.
  */
+enum { CTM_PROFILE_SERIAL = 0x100 };
 int ctm_profile_enable(ctm_ctx* ctx, int on);
 int ctm_profile_read(ctm_ctx* ctx, int cls, long long* launches, double* ms, double* flops);
 
@@ -244,6 +250,18 @@ int ctm_contract_test(int precision, long long M, long long N, long long K, cons
  * CTM_ERR_CUDA, CTM_ERR_NOCONV.
  */
 int ctm_truncated_svd_test(int path, const double* M, int rows, int cols, int k, double* U);
+
+/*
+ * Test hook for the orthonormalisation inside the projector factorisations (no
+ * counterpart in the paper; the mixed-precision subspace iteration that stands
+ * in for the truncated SVDs of Sec. IV, Fig. 4a, orthonormalises with it):
+ * Q (host, row-major rows x n) receives an orthonormal basis of the columns of
+ * the host row-major matrix Y (rows x n, n <= rows) from `passes` (1..8) FP64
+ * CholeskyQR passes, the first shifted (the library's fused cooperative kernel
+ * for n <= 512).  Allocates its own device memory; synchronous.  Errors:
+ * CTM_ERR_ARG, CTM_ERR_OOM, CTM_ERR_CUDA.
+ */
+int ctm_cholqr_test(const double* Y, int rows, int n, int passes, double* Q);
 
 /*
  * Batching of independent states (no counterpart in the paper: many iPEPS

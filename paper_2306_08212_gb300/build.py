@@ -8,7 +8,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libctm.so")
-SOURCES = ["ctm.cu", "gemm_f64.cu", "linalg.cu", "tc_gemm.cu", "noalloc.cu", "adjoint.cu"]
+SOURCES = ["ctm.cu", "gemm_f64.cu", "linalg.cu", "tc_gemm.cu", "noalloc.cu", "adjoint.cu",
+           "cholqr.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

@@ -1,0 +1,572 @@
+// Fused CholeskyQR in FP64: an orthonormal basis Q (row-major rows x n) of the
+// columns of Y (row-major rows x n) in ONE cooperative launch, every pass of
+// the method inside it, phases separated by bounded grid barriers.
+//
+// One pass (scaled CholeskyQR; Fukaya, Kannan, Nakatsukasa, Yamamoto &
+// Yanagisawa, SIAM J. Sci. Comput. 42, A477 (2020), for the shifted first pass):
+//   G  = X^T X                          Gram, 32 x 32 tiles x row chunks, partial
+//                                        tiles reduced in a fixed order (deterministic)
+//   G' = D^-1 G D^-1 (+ s I)            D = diag(sqrt(G_ii)); shift s on the first
+//                                        pass of an ill-conditioned input
+//   G' = L L^T                          right-looking blocked Cholesky, 32-wide
+//                                        panels; the diagonal block and its inverse
+//                                        on one warp
+//   Q  = X D^-1 L^-T                    blocked forward substitution, each CTA
+//                                        owning 16-row blocks (no barrier inside)
+// When G' is within kNearIdentity of the identity (max |G' - I|, decided on the
+// device from the reduced Gram), L^-T = I - U + O(e^2) with U the strict upper
+// triangle of G' - I: the error e^2 <= 1e-16 is below FP64 rounding, so that
+// pass skips the Cholesky and computes Q = X D^-1 (I - U) directly.
+//
+// Rank deficiency (unshifted passes): a pivot of the scaled Gram below tau marks
+// a column in the span of the earlier ones; its L column becomes e_k and, after a
+// pass that is neither the first nor the last, the column is replaced by
+// Gaussian values (counter-based SplitMix64 + Box-Muller) that the next pass
+// orthonormalises against the rest.
+//
+// FP64 on GB300 retires about two FMA per clock per SM, so every phase is
+// bound by FP64 issue: the Gram and the substitution each cost rows n^2 / 2 FMA,
+// spread over all SMs; the Cholesky costs n^3 / 6, most of it latency.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "ctm_internal.h"
+
+namespace ctm {
+
+namespace {
+
+constexpr int kCqThreads = 256;
+constexpr int kTb = 32;           // tile / panel width
+constexpr int kRowBlock = 16;     // rows per substitution block
+constexpr double kNearIdentity = 1e-8;
+constexpr long long kCqBarrierLimit = 4000000000ll;  // clocks (~2 s)
+constexpr int kCqMaxN = kCholqrMaxN;
+
+struct CqArgs {
+  const double* Y;
+  double* Q;
+  int rows, n, passes, shifted;
+  int nchunk, chunk_rows, npairs, T;
+  double* part;     // [nchunk][npairs][32 * 32]
+  double* G;        // n x n, lower triangle used
+  double* Linv;     // [T][32 * 32]
+  double* dscale;   // n
+  double* emax;     // [passes] max |G' - I| (bits of a non-negative double)
+  int* defmask;     // n
+  DevFlags* fl;     // this launch's own barrier words (inside the work buffer)
+  int* err_out;     // sticky error word of the caller (set on a barrier timeout)
+  int* floored;
+  unsigned long long seed;
+};
+
+__device__ __forceinline__ unsigned cq_ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned cq_atom_add_release(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
+               : "memory");
+  return old;
+}
+
+// Generation barrier over the whole grid with a clock limit; false once any
+// block has timed out (every block then returns).
+__device__ bool cq_barrier(DevFlags* fl) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned g = cq_ld_acquire(&fl->bar_gen);
+    const unsigned arrived = cq_atom_add_release(&fl->bar_count, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(&fl->bar_count, 0u);
+      cq_atom_add_release(&fl->bar_gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (cq_ld_acquire(&fl->bar_gen) == g) {
+        if (clock64() - t0 > kCqBarrierLimit) {
+          atomicExch(&fl->error, 1);
+          break;
+        }
+      }
+    }
+    s_ok = (*(volatile int*)&fl->error) == 0;
+  }
+  __syncthreads();
+  return s_ok;
+}
+
+__device__ __forceinline__ unsigned long long cq_splitmix64(unsigned long long z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double cq_gauss(unsigned long long seed, unsigned long long idx) {
+  const unsigned long long base = seed * 0xD1B54A32D192ED03ull + 2ull * idx;
+  const unsigned long long z1 = cq_splitmix64(base), z2 = cq_splitmix64(base + 1ull);
+  const double u1 = ((double)(z1 >> 11) + 1.0) * 0x1.0p-53;
+  const double u2 = (double)(z2 >> 11) * 0x1.0p-53;
+  return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+// (bi, bj), bi <= bj, of upper-triangle tile pair number `pair` (row-major order).
+__device__ __forceinline__ void pair_of(int pair, int T, int& bi, int& bj) {
+  int i = 0, start = 0;
+  while (pair >= start + (T - i)) {
+    start += T - i;
+    ++i;
+  }
+  bi = i;
+  bj = i + (pair - start);
+}
+
+__device__ __forceinline__ int pair_index(int bi, int bj, int T) {  // bi <= bj
+  return bi * T - bi * (bi - 1) / 2 + (bj - bi);
+}
+
+// Phase G: partial Gram tiles.  Thread (ty, tx) of a 16 x 16 layout owns the 2 x 2
+// outputs (2ty + a, 2tx + b) of the 32 x 32 tile.
+__device__ void gram_partials(const CqArgs& a, const double* __restrict__ X) {
+  __shared__ double As[kTb][kTb + 1];
+  __shared__ double Bs[kTb][kTb + 1];
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+  const int items = a.npairs * a.nchunk;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int pair = item % a.npairs, chunk = item / a.npairs;
+    int bi, bj;
+    pair_of(pair, a.T, bi, bj);
+    const int r0 = chunk * a.chunk_rows;
+    const int r1 = min(a.rows, r0 + a.chunk_rows);
+    double acc00 = 0.0, acc01 = 0.0, acc10 = 0.0, acc11 = 0.0;
+    for (int rs = r0; rs < r1; rs += kTb) {
+      __syncthreads();
+      for (int e = tid; e < kTb * kTb; e += kCqThreads) {
+        const int rr = e / kTb, cc = e % kTb;
+        const int r = rs + rr, ci = bi * kTb + cc, cj = bj * kTb + cc;
+        As[rr][cc] = (r < r1 && ci < a.n) ? X[(long long)r * a.n + ci] : 0.0;
+        Bs[rr][cc] = (r < r1 && cj < a.n) ? X[(long long)r * a.n + cj] : 0.0;
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int rr = 0; rr < kTb; ++rr) {
+        const double a0 = As[rr][2 * ty], a1 = As[rr][2 * ty + 1];
+        const double b0 = Bs[rr][2 * tx], b1 = Bs[rr][2 * tx + 1];
+        acc00 = fma(a0, b0, acc00);
+        acc01 = fma(a0, b1, acc01);
+        acc10 = fma(a1, b0, acc10);
+        acc11 = fma(a1, b1, acc11);
+      }
+    }
+    double* out = a.part + ((long long)chunk * a.npairs + pair) * (kTb * kTb);
+    out[(2 * ty) * kTb + 2 * tx] = acc00;
+    out[(2 * ty) * kTb + 2 * tx + 1] = acc01;
+    out[(2 * ty + 1) * kTb + 2 * tx] = acc10;
+    out[(2 * ty + 1) * kTb + 2 * tx + 1] = acc11;
+  }
+}
+
+__device__ __forceinline__ double gram_entry(const CqArgs& a, int i, int j) {  // any i, j
+  if (i > j) {
+    const int t = i;
+    i = j;
+    j = t;
+  }
+  const int bi = i / kTb, bj = j / kTb;
+  const long long off =
+      (long long)pair_index(bi, bj, a.T) * (kTb * kTb) + (i % kTb) * kTb + (j % kTb);
+  double s = 0.0;
+  for (int c = 0; c < a.nchunk; ++c) s += a.part[(long long)c * a.npairs * (kTb * kTb) + off];
+  return s;
+}
+
+// Phase R: G' (lower triangle) = D^-1 G D^-1 + shift I, D, and max |G' - I|.
+__device__ void reduce_scale(const CqArgs& a, double shift, double* emax) {
+  const long long nn = (long long)a.n * a.n;
+  double local = 0.0;
+  for (long long e = blockIdx.x * (long long)kCqThreads + threadIdx.x; e < nn;
+       e += (long long)gridDim.x * kCqThreads) {
+    const int i = (int)(e / a.n), j = (int)(e % a.n);
+    if (j > i) continue;
+    const double gii = gram_entry(a, i, i), gjj = gram_entry(a, j, j);
+    const double di = gii > 0.0 ? sqrt(gii) : 1.0, dj = gjj > 0.0 ? sqrt(gjj) : 1.0;
+    double v = gram_entry(a, i, j) / (di * dj);
+    if (i == j) {
+      v += shift;
+      a.dscale[i] = di;
+    }
+    a.G[(long long)i * a.n + j] = v;
+    local = fmax(local, fabs(v - (i == j ? 1.0 : 0.0)));
+  }
+  for (int o = 16; o > 0; o >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, o));
+  if ((threadIdx.x & 31) == 0 && local > 0.0)
+    atomicMax(reinterpret_cast<unsigned long long*>(emax),
+              (unsigned long long)__double_as_longlong(local));
+}
+
+// Diagonal block p: Cholesky in place (lower) and its inverse into Linv[p], on
+// warp 0 of the calling block.  Pivot rules: shifted pass -> floor at `floor`
+// (counted); unshifted passes -> a pivot <= tau marks a dependent column.
+__device__ void diag_factor(const CqArgs& a, int p, double floor, double tau, bool use_mask) {
+  __shared__ double L[kTb][kTb + 1];
+  __shared__ double X[kTb][kTb + 1];
+  __shared__ double rinv[kTb];
+  const int lane = threadIdx.x;
+  const int j0 = p * kTb, jb = min(kTb, a.n - j0);
+  if (threadIdx.x < 32) {
+    for (int j = 0; j < kTb; ++j)
+      L[lane][j] = (lane < jb && j < jb && j <= lane) ? a.G[(long long)(j0 + lane) * a.n + j0 + j]
+                                                      : 0.0;
+    __syncwarp();
+    for (int k = 0; k < jb; ++k) {
+      double dkk = L[k][k];
+      bool dep = false, floored = false;
+      if (use_mask && !(dkk > tau)) {
+        dep = true;
+        dkk = 1.0;
+      } else if (!(dkk > floor)) {
+        dkk = floor;
+        floored = true;
+      }
+      const double piv = sqrt(dkk);
+      __syncwarp();
+      if (lane == k) {
+        L[k][k] = piv;
+        rinv[k] = 1.0 / piv;
+        if (dep) a.defmask[j0 + k] = 1;
+        if (floored) atomicAdd(a.floored, 1);
+      }
+      if (lane > k && lane < jb) L[lane][k] = dep ? 0.0 : L[lane][k] / piv;
+      __syncwarp();
+      if (lane > k && lane < jb) {
+        const double lik = L[lane][k];
+        for (int j = k + 1; j <= lane; ++j) L[lane][j] = fma(-lik, L[j][k], L[lane][j]);
+      }
+      __syncwarp();
+    }
+    // inverse, column `lane`: x_i = (delta_{i,lane} - sum_{lane <= k < i} L_ik x_k) / L_ii
+    for (int i = 0; i < kTb; ++i) {
+      double v = 0.0;
+      if (lane < jb && i < jb && i >= lane) {
+        double acc = (i == lane) ? 1.0 : 0.0;
+        for (int k = lane; k < i; ++k) acc = fma(-L[i][k], X[k][lane], acc);
+        v = acc * rinv[i];
+      }
+      X[i][lane] = v;
+      __syncwarp();
+    }
+    for (int i = 0; i < kTb; ++i) {
+      if (i < jb && lane < jb) a.G[(long long)(j0 + i) * a.n + j0 + lane] = lane <= i ? L[i][lane] : 0.0;
+      a.Linv[(long long)p * kTb * kTb + i * kTb + lane] = X[i][lane];
+    }
+  }
+}
+
+// Panel p: L_ip = G'_ip Linv_pp^T for block rows i > p; items are 8-row groups.
+__device__ void panel_solve(const CqArgs& a, int p) {
+  __shared__ double Li[kTb][kTb + 1];
+  __shared__ double Gr[8][kTb + 1];
+  const int tid = threadIdx.x;
+  const int j0 = p * kTb, jb = min(kTb, a.n - j0);
+  const int r_lo = j0 + jb;
+  const int groups = (a.n - r_lo + 7) / 8;
+  for (int item = blockIdx.x; item < groups; item += gridDim.x) {
+    const int r0 = r_lo + item * 8;
+    __syncthreads();
+    for (int e = tid; e < kTb * kTb; e += kCqThreads)
+      Li[e / kTb][e % kTb] = a.Linv[(long long)p * kTb * kTb + e];
+    {
+      const int rr = tid / kTb, cc = tid % kTb;
+      const int r = r0 + rr;
+      Gr[rr][cc] = (r < a.n && cc < jb) ? a.G[(long long)r * a.n + j0 + cc] : 0.0;
+    }
+    __syncthreads();
+    const int rr = tid / kTb, cc = tid % kTb;
+    double acc = 0.0;
+#pragma unroll 8
+    for (int k = 0; k < kTb; ++k) acc = fma(Gr[rr][k], Li[cc][k], acc);
+    const int r = r0 + rr;
+    if (r < a.n && cc < jb) a.G[(long long)r * a.n + j0 + cc] = acc;
+  }
+}
+
+// Trailing update after panel p: G'_ij -= L_ip L_jp^T for p < bj <= bi (block
+// coordinates), lower blocks only; items are (block pair, 8-row group).
+__device__ void trailing_update(const CqArgs& a, int p) {
+  __shared__ double Lj[kTb][kTb + 1];
+  __shared__ double Lr[8][kTb + 1];
+  const int tid = threadIdx.x;
+  const int j0 = p * kTb, jb = min(kTb, a.n - j0);
+  const int nb = a.T - p - 1;  // remaining block rows/cols
+  const int pairs = nb * (nb + 1) / 2;
+  const int items = pairs * 4;
+  for (int item = blockIdx.x; item < items; item += gridDim.x) {
+    const int pr = item / 4, g = item % 4;
+    int ci, cj;  // ci <= cj in 0..nb-1 : block col = p+1+ci, block row = p+1+cj
+    pair_of(pr, nb, ci, cj);
+    const int bc = p + 1 + ci, br = p + 1 + cj;
+    const int r0 = br * kTb + g * 8;
+    __syncthreads();
+    for (int e = tid; e < kTb * kTb; e += kCqThreads) {
+      const int rr = e / kTb, kk = e % kTb;
+      const int r = bc * kTb + rr;
+      Lj[rr][kk] = (r < a.n && kk < jb) ? a.G[(long long)r * a.n + j0 + kk] : 0.0;
+    }
+    {
+      const int rr = tid / kTb, kk = tid % kTb;
+      const int r = r0 + rr;
+      Lr[rr][kk] = (r < a.n && kk < jb) ? a.G[(long long)r * a.n + j0 + kk] : 0.0;
+    }
+    __syncthreads();
+    const int rr = tid / kTb, cc = tid % kTb;
+    const int r = r0 + rr, col = bc * kTb + cc;
+    if (r < a.n && col < a.n && col <= r) {
+      double acc = 0.0;
+#pragma unroll 8
+      for (int k = 0; k < kTb; ++k) acc = fma(Lr[rr][k], Lj[cc][k], acc);
+      a.G[(long long)r * a.n + col] -= acc;
+    }
+  }
+}
+
+// Phase T: Q = X D^-1 L^-T (full) or Q = X D^-1 (I - U) (near identity) for the
+// 16-row blocks this CTA owns; then, when asked, flagged columns become Gaussian.
+__device__ void substitute(const CqArgs& a, const double* __restrict__ X, bool near_id,
+                           bool refill, unsigned long long seed) {
+  extern __shared__ double dyn[];
+  double* Xs = dyn;                      // [kRowBlock][n] scaled input rows
+  double* Qs = dyn + kRowBlock * a.n;    // [kRowBlock][n] output rows
+  __shared__ double Lt[kTb][kTb + 1];    // a 32 x 32 tile of L (or U^T)
+  __shared__ double Tt[kRowBlock][kTb + 1];
+  const int tid = threadIdx.x;
+  const int nblk = (a.rows + kRowBlock - 1) / kRowBlock;
+  for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+    const int r0 = blk * kRowBlock;
+    __syncthreads();
+    for (int e = tid; e < kRowBlock * a.n; e += kCqThreads) {
+      const int rr = e / a.n, cc = e % a.n;
+      const int r = r0 + rr;
+      Xs[e] = r < a.rows ? X[(long long)r * a.n + cc] / a.dscale[cc] : 0.0;
+    }
+    __syncthreads();
+    for (int p = 0; p < a.T; ++p) {
+      const int j0 = p * kTb, jb = min(kTb, a.n - j0);
+      // thread -> (row rr, col cc) of the 16 x 32 panel block, two per thread
+      const int cc = tid % kTb, rr0 = tid / kTb;  // rows rr0 and rr0 + 8
+      double acc0 = 0.0, acc1 = 0.0;
+      const double* src = near_id ? Xs : Qs;
+      for (int k0 = 0; k0 < j0; k0 += kTb) {
+        __syncthreads();
+        for (int e = tid; e < kTb * kTb; e += kCqThreads) {
+          const int i = e / kTb, k = e % kTb;  // Lt[i][k] = L[j0 + i][k0 + k]
+          Lt[i][k] = (i < jb) ? a.G[(long long)(j0 + i) * a.n + k0 + k] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < kTb; ++k) {
+          const double l = Lt[cc][k];
+          acc0 = fma(src[rr0 * a.n + k0 + k], l, acc0);
+          acc1 = fma(src[(rr0 + 8) * a.n + k0 + k], l, acc1);
+        }
+      }
+      if (near_id) {
+        // Q_j = xs_j - sum_{k < j} xs_k E_jk, including k inside this panel
+        __syncthreads();
+        for (int e = tid; e < kTb * kTb; e += kCqThreads) {
+          const int i = e / kTb, k = e % kTb;
+          Lt[i][k] = (i < jb && k < i) ? a.G[(long long)(j0 + i) * a.n + j0 + k] : 0.0;
+        }
+        __syncthreads();
+        for (int k = 0; k < kTb; ++k) {
+          const double l = Lt[cc][k];
+          acc0 = fma(Xs[rr0 * a.n + j0 + k], l, acc0);
+          acc1 = fma(Xs[(rr0 + 8) * a.n + j0 + k], l, acc1);
+        }
+        if (cc < jb) {
+          Qs[rr0 * a.n + j0 + cc] = Xs[rr0 * a.n + j0 + cc] - acc0;
+          Qs[(rr0 + 8) * a.n + j0 + cc] = Xs[(rr0 + 8) * a.n + j0 + cc] - acc1;
+        }
+      } else {
+        // T = xs_panel - Q_{<p} L_{p,<p}^T, then Q_panel = T Linv_pp^T
+        Tt[rr0][cc] = cc < jb ? Xs[rr0 * a.n + j0 + cc] - acc0 : 0.0;
+        Tt[rr0 + 8][cc] = cc < jb ? Xs[(rr0 + 8) * a.n + j0 + cc] - acc1 : 0.0;
+        __syncthreads();
+        for (int e = tid; e < kTb * kTb; e += kCqThreads)
+          Lt[e / kTb][e % kTb] = a.Linv[(long long)p * kTb * kTb + e];
+        __syncthreads();
+        double q0 = 0.0, q1 = 0.0;
+#pragma unroll 8
+        for (int k = 0; k < kTb; ++k) {
+          const double l = Lt[cc][k];
+          q0 = fma(Tt[rr0][k], l, q0);
+          q1 = fma(Tt[rr0 + 8][k], l, q1);
+        }
+        if (cc < jb) {
+          Qs[rr0 * a.n + j0 + cc] = q0;
+          Qs[(rr0 + 8) * a.n + j0 + cc] = q1;
+        }
+      }
+      __syncthreads();
+    }
+    for (int e = tid; e < kRowBlock * a.n; e += kCqThreads) {
+      const int rr = e / a.n, cc = e % a.n;
+      const int r = r0 + rr;
+      if (r >= a.rows) continue;
+      double v = Qs[e];
+      if (refill && a.defmask[cc])
+        v = cq_gauss(seed, (unsigned long long)cc * a.rows + r);
+      a.Q[(long long)r * a.n + cc] = v;
+    }
+  }
+}
+
+__device__ bool cholqr_passes(const CqArgs& a, double u);
+
+__global__ void __launch_bounds__(kCqThreads, 1) cholqr_kernel(CqArgs a) {
+  const double u = 1.1102230246251565e-16;
+  const bool ok = cholqr_passes(a, u);
+  if (!ok && blockIdx.x == 0 && threadIdx.x == 0 && a.err_out) atomicExch(a.err_out, 1);
+}
+
+__device__ bool cholqr_passes(const CqArgs& a, double u) {
+  for (int pass = 0; pass < a.passes; ++pass) {
+    const double* X = pass == 0 ? a.Y : a.Q;
+    const bool shift_pass = pass == 0 && a.shifted;
+    gram_partials(a, X);
+    if (!cq_barrier(a.fl)) return false;
+    // the mask of the previous pass has been read by every block by now
+    for (int j = blockIdx.x * kCqThreads + threadIdx.x; j < a.n; j += gridDim.x * kCqThreads)
+      a.defmask[j] = 0;
+    const double shift =
+        shift_pass ? 11.0 * ((double)a.rows * a.n + (double)a.n * (a.n + 1)) * u * a.n : 0.0;
+    reduce_scale(a, shift, a.emax + pass);
+    if (!cq_barrier(a.fl)) return false;
+    // every block must take the same branch (the barrier count depends on it):
+    // thread 0 reads the reduced maximum with an acquire load and broadcasts it
+    __shared__ double s_e;
+    if (threadIdx.x == 0) {
+      unsigned long long bits;
+      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];"
+                   : "=l"(bits)
+                   : "l"(a.emax + pass)
+                   : "memory");
+      s_e = __longlong_as_double((long long)bits);
+    }
+    __syncthreads();
+    const double e = s_e;
+    const bool near_id = !shift_pass && e < kNearIdentity;
+    if (!near_id) {
+      for (int p = 0; p < a.T; ++p) {
+        if (blockIdx.x == 0) diag_factor(a, p, 1e-28, 1e-12, !shift_pass && pass > 0);
+        if (!cq_barrier(a.fl)) return false;
+        panel_solve(a, p);
+        if (!cq_barrier(a.fl)) return false;
+        if (p + 1 < a.T) {
+          trailing_update(a, p);
+          if (!cq_barrier(a.fl)) return false;
+        }
+      }
+    }
+    const bool refill = !near_id && pass > 0 && pass + 1 < a.passes;
+    substitute(a, X, near_id, refill, a.seed + (unsigned long long)pass);
+    if (!cq_barrier(a.fl)) return false;
+  }
+  return true;
+}
+
+// Work layout (doubles): Gram partials | G' (n x n) | diagonal-block inverses |
+// D | max |G' - I| per pass (8) | dependent-column mask (n ints) | barrier words.
+void cholqr_layout(int rows, int n, int nsm, int& T, int& npairs, int& nchunk, int& chunk_rows) {
+  T = (n + kTb - 1) / kTb;
+  npairs = T * (T + 1) / 2;
+  nchunk = (2 * nsm + npairs - 1) / npairs;
+  const int max_chunks = (rows + kTb - 1) / kTb;
+  if (nchunk > max_chunks) nchunk = max_chunks;
+  if (nchunk < 1) nchunk = 1;
+  chunk_rows = ((rows + nchunk - 1) / nchunk + kTb - 1) / kTb * kTb;
+  nchunk = (rows + chunk_rows - 1) / chunk_rows;
+}
+
+int cholqr_sm_count() {
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return nsm;
+}
+
+}  // namespace
+
+size_t cholqr_work_doubles(int rows, int n) {
+  const int nsm = cholqr_sm_count();
+  int T, npairs, nchunk, chunk_rows;
+  cholqr_layout(rows, n, nsm > 0 ? nsm : 1, T, npairs, nchunk, chunk_rows);
+  return (size_t)nchunk * npairs * kTb * kTb + (size_t)n * n + (size_t)T * kTb * kTb + n + 8 +
+         (size_t)(n + 1) / 2 + 8;
+}
+
+int cholqr_fused(cudaStream_t s, const double* Y, double* Q, int rows, int n, int passes,
+                 bool shifted, double* work, int* err_word, int* floored, unsigned long long seed,
+                 long long* launches, cudaEvent_t t0, cudaEvent_t t1) {
+  if (n < 1 || n > kCqMaxN || rows < 1 || passes < 1 || passes > 8) return -1;
+  const int nsm = cholqr_sm_count();
+  if (nsm < 1) return -3;
+  CqArgs a;
+  a.Y = Y;
+  a.Q = Q;
+  a.rows = rows;
+  a.n = n;
+  a.passes = passes;
+  a.shifted = shifted ? 1 : 0;
+  cholqr_layout(rows, n, nsm, a.T, a.npairs, a.nchunk, a.chunk_rows);
+  double* w = work;
+  a.part = w;
+  w += (size_t)a.nchunk * a.npairs * kTb * kTb;
+  a.G = w;
+  w += (size_t)n * n;
+  a.Linv = w;
+  w += (size_t)a.T * kTb * kTb;
+  a.dscale = w;
+  w += n;
+  a.emax = w;
+  w += 8;
+  a.defmask = reinterpret_cast<int*>(w);
+  w += (n + 1) / 2;
+  a.fl = reinterpret_cast<DevFlags*>(w);
+  static_assert(sizeof(DevFlags) <= 8 * sizeof(double), "DevFlags must fit its slot");
+  a.err_out = err_word;
+  a.floored = floored;
+  a.seed = seed;
+  const size_t dyn = sizeof(double) * 2 * kRowBlock * (size_t)n;
+  static int attr_dev = -1;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return -3;
+  if (attr_dev != dev) {
+    if (cudaFuncSetAttribute(cholqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * 2 * kRowBlock * kCqMaxN)) != cudaSuccess)
+      return -3;
+    attr_dev = dev;
+  }
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cholqr_kernel, kCqThreads, dyn) !=
+          cudaSuccess ||
+      per_sm < 1)
+    return -3;
+  // this launch's barrier words and per-pass maxima start at zero
+  if (cudaMemsetAsync(a.emax, 0, 8 * sizeof(double), s) != cudaSuccess) return -3;
+  if (cudaMemsetAsync(a.fl, 0, sizeof(DevFlags), s) != cudaSuccess) return -3;
+  void* args[] = {&a};
+  if (launch_cooperative(reinterpret_cast<const void*>(cholqr_kernel), dim3(nsm),
+                         dim3(kCqThreads), args, dyn, s, t0, t1) != cudaSuccess)
+    return -3;
+  ++*launches;
+  return 0;
+}
+
+}  // namespace ctm

@@ -32,13 +32,17 @@ void ck(cudaError_t e, const char* what) {
   if (e != cudaSuccess) fail(CTM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-constexpr int kExactSvdMax = 2048;  // exact one-sided Jacobi up to this size
+constexpr int kExactSvdMax = 1024;  // exact one-sided Jacobi up to this size
 constexpr int kFastMinSide = 0;  // mixed precision: subspace iteration for every size
 constexpr int kMinOversample = 16;  // randomized range finder: extra columns (at least)
 constexpr int kMaxPowerIters = 40;  // randomized range finder: subspace iteration cap
 constexpr int kCapturedPowerIters = 4;  // inside a stream capture (no host check possible)
 constexpr double kSubspaceTol = 1e-12;  // RMS sine of the principal angles between sweeps
 constexpr int kMaxSweeps = 60;
+// kernel classes timed by ctm_profile_enable: 0 FP64 contraction, 1 TF32 and
+// 2 BF16 tensor-core contraction, 3 Jacobi, 4 fused CholeskyQR
+constexpr int kProfClasses = 5;
+constexpr int kProfMaskAll = (1 << kProfClasses) - 1;
 
 }  // namespace
 
@@ -65,8 +69,9 @@ struct ctm_ctx {
     double ms = 0.0, flops = 0.0;
   };
   int prof_mask = 0;  // bit cls set: time that class
-  ProfClass prof[4];
-  long long prof_seen[4] = {0, 0, 0, 0};  // launches of each class (for sampling)
+  bool prof_serial = false;  // calibration: one stream, eager launches (no graphs)
+  ProfClass prof[kProfClasses];
+  long long prof_seen[kProfClasses] = {};  // launches of each class (for sampling)
   struct CacheEntry {  // warm start of the mixed-precision subspace iteration
     double* p = nullptr;
     int rows = 0, k = 0;
@@ -493,6 +498,10 @@ Tmp left_svd(ctm_ctx* c, const double* M, int rows, int cols, int k) {
 double subspace_change(ctm_ctx* c, const double* Uold, const double* Unew, int rows, int ld,
                        int k);
 
+// Randomized subspace iteration run to convergence (defined with the
+// CholeskyQR it orthonormalises with).
+Tmp left_svd_subspace(ctm_ctx* c, const double* M, int rows, int cols, int k);
+
 Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k, int path) {
   if (k >= rows) return identity(c, rows);
   if (k > std::min(rows, cols)) fail(CTM_ERR_ARG, "truncation rank exceeds the matrix rank bound");
@@ -525,93 +534,7 @@ Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k, int pa
     dfree(c, perm);
     return U;
   }
-  const int l = std::min(k + std::max(kMinOversample, k / 2), std::min(rows, cols));
-  LegMap Mrow, Mcol;
-  // M(i, j) at i*cols + j
-  push(Mrow, rows, cols);
-  push(Mcol, cols, 1);
-  Tmp Om(c, {cols, l});
-  ck(gaussian_fill(c->stream, Om.t.p, (long long)cols * l, c->seed++), "gaussian");
-  ++c->launches;
-  // Y = M Omega, stored column-major (rows x l)
-  auto times_M = [&](const double* Rrow /* row-major cols x l */) {
-    Tmp Y(c, {l, rows});
-    LegMap Bk, Bn, Cm, Cn;
-    push(Bk, cols, l);
-    push(Bn, l, 1);
-    push(Cm, rows, 1);
-    push(Cn, l, rows);
-    {
-      ProfScope ps(c, 0, 2.0 * rows * l * cols);
-      ck(gemm_f64(c->stream, rows, l, cols, 1.0, M, Mrow, Mcol, Rrow, Bk, Bn, 0.0, Y.t.p, Cm, Cn),
-         "M Q");
-    }
-    ++c->launches;
-    return Y;
-  };
-  // Z = M^T Q (Q row-major rows x l), stored column-major (cols x l)
-  auto times_Mt = [&](const double* Qrow) {
-    Tmp Z(c, {l, cols});
-    LegMap Am, Ak, Bk, Bn, Cm, Cn;
-    push(Am, cols, 1);
-    push(Ak, rows, cols);
-    push(Bk, rows, l);
-    push(Bn, l, 1);
-    push(Cm, cols, 1);
-    push(Cn, l, cols);
-    {
-      ProfScope ps(c, 0, 2.0 * rows * l * cols);
-      ck(gemm_f64(c->stream, cols, l, rows, 1.0, M, Am, Ak, Qrow, Bk, Bn, 0.0, Z.t.p, Cm, Cn),
-         "M^T Q");
-    }
-    ++c->launches;
-    return Z;
-  };
-  Tmp Y = times_M(Om.t.p);
-  Om.release();
-  jacobi(c, Y.t.p, rows, l, nullptr);
-  Tmp Q = sorted_unit_columns(c, Y.t.p, rows, l, l);
-  Y.release();
-  // Subspace iteration Q <- orth(M orth(M^T Q)).  After each sweep the columns
-  // of Q, sorted by norm before normalisation, are the left singular vectors of
-  // M orth(M^T Q); the sweeps stop when the span of their leading k no longer
-  // moves (kSubspaceTol), or after kMaxPowerIters.  Inside a stream capture the
-  // host cannot look, so a fixed count runs.
-  const int max_iters = c->capturing ? kCapturedPowerIters : kMaxPowerIters;
-  double prev_moved = INFINITY;
-  for (int it = 0; it < max_iters; ++it) {
-    Tmp Z = times_Mt(Q.t.p);
-    jacobi(c, Z.t.p, cols, l, nullptr);
-    Tmp Qz = sorted_unit_columns(c, Z.t.p, cols, l, l);
-    Z.release();
-    Tmp Y2 = times_M(Qz.t.p);
-    Qz.release();
-    jacobi(c, Y2.t.p, rows, l, nullptr);
-    Tmp Qn = sorted_unit_columns(c, Y2.t.p, rows, l, l);
-    Y2.release();
-    const bool check = !c->capturing;
-    const double moved = check ? subspace_change(c, Q.t.p, Qn.t.p, rows, l, k) : 1.0;
-    Q = std::move(Qn);
-    if (trace_on() && check)
-      std::fprintf(stderr, "[ctm] range finder %dx%d k=%d l=%d sweep %d: subspace moved %.3e\n",
-                   rows, cols, k, l, it + 1, moved);
-    // converged, or down at the rounding floor (no longer shrinking)
-    if (moved < kSubspaceTol || (moved < 1e-10 && moved > 0.9 * prev_moved)) break;
-    prev_moved = moved;
-  }
-  // Rayleigh-Ritz: Z = M^T Q = (Q^T M)^T; Jacobi with V gives Q^T M = V S W^T
-  Tmp Z = times_Mt(Q.t.p);
-  Tmp V(c, {l, l});
-  jacobi(c, Z.t.p, cols, l, V.t.p);
-  Tmp sig(c, {l});
-  int* perm = (int*)dalloc(c, (l + 1) / 2 + 1);
-  ck(column_norms_sorted(c->stream, Z.t.p, cols, l, sig.t.p, perm), "norms");
-  Tmp Vk(c, {l, k});
-  ck(gather_sorted_columns(c->stream, Vk.t.p, l, k, nullptr, V.t.p, sig.t.p, perm), "gather");
-  c->launches += 3;
-  dfree(c, perm);
-  Ten Qv = view(Q.t, {rows, l});
-  return ein64(c, "ic,cr->ir", Qv, Vk.t);
+  return left_svd_subspace(c, M, rows, cols, k);
 }
 
 double subspace_change(ctm_ctx* c, const double* Uold, const double* Unew, int rows, int ld,
@@ -693,8 +616,33 @@ void gemm_mixed(ctm_ctx* c, long long M, long long N, long long K, const double*
 // (i, j) sits at Y[i * ys_r + j * ys_c], by `passes` CholeskyQR passes in FP64:
 // G = Q^T Q, column scaling D, G' = D^-1 G D^-1 (+ shift on the first pass),
 // blocked Cholesky G' = L L^T (32-wide panels, updates as GEMMs), Q <- Q D^-1 L^-T.
+Tmp cholqr_chain(ctm_ctx* c, const double* Y, long long ys_r, long long ys_c, int rows, int n,
+                 int passes);
+
 Tmp cholqr(ctm_ctx* c, const double* Y, long long ys_r, long long ys_c, int rows, int n,
            int passes) {
+  if (n > kCholqrMaxN || ys_r != n || ys_c != 1 || rows < n)
+    return cholqr_chain(c, Y, ys_r, ys_c, rows, n, passes);
+  Tmp Q(c, {rows, n});
+  Tmp W(c, {(int)cholqr_work_doubles(rows, n)});
+  {
+    const double flops = passes * (2.0 * rows * n * (double)n + (double)n * n * n / 3.0);
+    // the timing events bracket the kernel on the cooperative stream
+    ProfScope ps(c, 4, flops, true);
+    const int rc = cholqr_fused(c->stream, Y, Q.t.p, rows, n, passes, true, W.t.p,
+                                &c->flags->error, c->floored, c->seed, &c->launches, ps.ev0(),
+                                ps.ev1());
+    c->seed += passes;
+    if (rc != 0) fail(CTM_ERR_CUDA, "fused CholeskyQR launch failed");
+  }
+  check_finite(c, Q.t, "cholqr");
+  return Q;
+}
+
+// The same passes as a chain of separate launches (blocked Cholesky with 32-wide
+// panels, updates as FP64 GEMMs); for n above the fused kernel's limit.
+Tmp cholqr_chain(ctm_ctx* c, const double* Y, long long ys_r, long long ys_c, int rows, int n,
+                 int passes) {
   constexpr int NB = 32;
   const int nblk = (n + NB - 1) / NB;
   Tmp Q(c, {rows, n});
@@ -758,6 +706,80 @@ Tmp cholqr(ctm_ctx* c, const double* Y, long long ys_r, long long ys_c, int rows
   }
   dfree(c, defmask);
   return Q;
+}
+
+// FP64 truncated SVD for large matrices: randomized subspace iteration (Halko,
+// Martinsson & Tropp, SIAM Rev. 53, 217 (2011)) with oversampling
+// l = k + max(16, k/2), every iterate orthonormalised by the fused CholeskyQR,
+// and a Rayleigh-Ritz step after each sweep: with Z = M^T Q = Qz R (CholeskyQR
+// of Z, R = Qz^T Z), Q^T M = R^T Qz^T, so the left singular vectors of Q^T M
+// are the right singular vectors V of the l x l matrix R (one-sided Jacobi) and
+// the Ritz vectors are U = Q V.  The sweeps stop when the span of the leading k
+// Ritz vectors no longer moves (RMS principal-angle sine < kSubspaceTol, or
+// stagnation at the rounding floor) or after kMaxPowerIters; inside a stream
+// capture the host cannot look, so kCapturedPowerIters sweeps run.
+Tmp left_svd_subspace(ctm_ctx* c, const double* M, int rows, int cols, int k) {
+  const int l = std::min(k + std::max(kMinOversample, k / 2), std::min(rows, cols));
+  // Y = M X with X row-major cols x l: Y row-major rows x l
+  auto times_M = [&](const double* X) {
+    Tmp Y(c, {rows, l});
+    gemm64(c, rows, l, cols, 1.0, M, lm1(rows, cols), lm1(cols, 1), X, lm1(cols, l), lm1(l, 1),
+           0.0, Y.t.p, lm1(rows, l), lm1(l, 1));
+    return Y;
+  };
+  // Z = M^T Q with Q row-major rows x l: Z row-major cols x l
+  auto times_Mt = [&](const double* Qr) {
+    Tmp Z(c, {cols, l});
+    gemm64(c, cols, l, rows, 1.0, M, lm1(cols, 1), lm1(rows, cols), Qr, lm1(rows, l), lm1(l, 1),
+           0.0, Z.t.p, lm1(cols, l), lm1(l, 1));
+    return Z;
+  };
+  Tmp Q;
+  {
+    Tmp Om(c, {cols, l});
+    ck(gaussian_fill(c->stream, Om.t.p, (long long)cols * l, c->seed++), "gaussian");
+    ++c->launches;
+    Tmp Y = times_M(Om.t.p);
+    Q = cholqr(c, Y.t.p, l, 1, rows, l, 3);
+  }
+  const int max_iters = c->capturing ? kCapturedPowerIters : kMaxPowerIters;
+  double prev_moved = INFINITY;
+  Tmp Uk;
+  for (int it = 0; it < max_iters; ++it) {
+    Tmp Z = times_Mt(Q.t.p);
+    Tmp Qz = cholqr(c, Z.t.p, l, 1, cols, l, 3);
+    // R = Qz^T Z (l x l), stored column-major for Jacobi on its columns
+    Tmp Rc(c, {l, l});
+    gemm64(c, l, l, cols, 1.0, Qz.t.p, lm1(l, 1), lm1(cols, l), Z.t.p, lm1(cols, l), lm1(l, 1),
+           0.0, Rc.t.p, lm1(l, 1), lm1(l, l));
+    Z.release();
+    Tmp V(c, {l, l});
+    jacobi(c, Rc.t.p, l, l, V.t.p);
+    Tmp Vk;
+    {
+      Tmp sig(c, {l});
+      int* perm = (int*)dalloc(c, (l + 1) / 2 + 1);
+      ck(column_norms_sorted(c->stream, Rc.t.p, l, l, sig.t.p, perm), "norms");
+      Vk = Tmp(c, {l, k});
+      ck(gather_sorted_columns(c->stream, Vk.t.p, l, k, nullptr, V.t.p, sig.t.p, perm), "gather");
+      c->launches += 3;
+      dfree(c, perm);
+    }
+    Tmp Un = ein64(c, "ic,cr->ir", Q.t, Vk.t);
+    const bool check = !c->capturing && it > 0;
+    const double moved = check ? subspace_change(c, Uk.t.p, Un.t.p, rows, k, k) : 1.0;
+    Uk = std::move(Un);
+    if (trace_on() && check)
+      std::fprintf(stderr, "[ctm] subspace iteration %dx%d k=%d l=%d sweep %d: moved %.3e\n",
+                   rows, cols, k, l, it + 1, moved);
+    // converged, or down at the rounding floor (no longer shrinking)
+    if (moved < kSubspaceTol || (moved < 1e-10 && moved > 0.9 * prev_moved)) break;
+    prev_moved = moved;
+    if (it + 1 == max_iters) break;
+    Tmp Y = times_M(Qz.t.p);
+    Q = cholqr(c, Y.t.p, l, 1, rows, l, 3);
+  }
+  return Uk;
 }
 
 constexpr int kColdIters = 2;  // power iterations without a cached subspace
@@ -843,8 +865,8 @@ void commit(ctm_ctx* c, int kind, int k, int x, int r, const Ten& src) {
 // Only when every factorisation of the move takes the fast path (no Jacobi,
 // whose device flags a context shares between its launches).
 bool can_fork(ctm_ctx* c) {
-  return c->precision != CTM_FP64 && c->side[0] != nullptr && c->chi * c->D > kFastMinSide &&
-         c->chip * c->D > kFastMinSide;
+  return c->precision != CTM_FP64 && c->side[0] != nullptr && !c->prof_serial &&
+         c->chi * c->D > kFastMinSide && c->chip * c->D > kFastMinSide;
 }
 
 cudaEvent_t fork_event(ctm_ctx* c) {
@@ -1167,7 +1189,8 @@ bool graph_eligible(ctm_ctx* c, int mode) {
     off = (e && *e && *e != '0') ? 1 : 0;
   }
   return !off && c->graphs_ok && c->stream != nullptr && c->precision != CTM_FP64 &&
-         mode == CTM_REDUCED_SEQUENTIAL && !trace_on() && !check_on() && all_bonds_at(c, c->chi);
+         !c->prof_serial && mode == CTM_REDUCED_SEQUENTIAL && !trace_on() && !check_on() &&
+         all_bonds_at(c, c->chi);
 }
 
 // Eager issue of one move (no host synchronisation).
@@ -2051,6 +2074,32 @@ int ctm_truncated_svd_test(int path, const double* M, int rows, int cols, int k,
   return rc;
 }
 
+int ctm_cholqr_test(const double* Y, int rows, int n, int passes, double* Q) {
+  if (!Y || !Q || rows < 1 || n < 1 || n > rows || passes < 1 || passes > 8) return CTM_ERR_ARG;
+  ctm_ctx* c = new (std::nothrow) ctm_ctx;
+  if (!c) return CTM_ERR_OOM;
+  int rc = guarded(c, [&] {
+    void* f = nullptr;
+    ck(cudaMalloc(&f, sizeof(DevFlags)), "flags");
+    c->owned.push_back(f);
+    c->flags = (DevFlags*)f;
+    ck(cudaMemset(c->flags, 0, sizeof(DevFlags)), "flags");
+    c->floored = (int*)owned_alloc(c, 1);
+    ck(cudaMemset(c->floored, 0, 2 * sizeof(int)), "floored");
+    if (!coop_stream()) fail(CTM_ERR_CUDA, "cooperative stream");
+    double* dY = owned_alloc(c, (long long)rows * n);
+    ck(cudaMemcpy(dY, Y, sizeof(double) * (size_t)rows * n, cudaMemcpyHostToDevice), "h2d");
+    Tmp Qd = cholqr(c, dY, n, 1, rows, n, passes);
+    ck(cudaMemcpyAsync(Q, Qd.t.p, sizeof(double) * (size_t)rows * n, cudaMemcpyDeviceToHost,
+                       c->stream),
+       "d2h");
+    Qd.release();
+    check_flags(c);
+  });
+  ctm_free(c);
+  return rc;
+}
+
 int ctm_profile_enable(ctm_ctx* c, int on) {
   if (!c) return CTM_ERR_ARG;
   return guarded(c, [&] {
@@ -2059,13 +2108,16 @@ int ctm_profile_enable(ctm_ctx* c, int on) {
       pc.count = 0;
       pc.ms = pc.flops = 0.0;
     }
-    if ((on & 0xF) != c->prof_mask) drop_graphs(c);  // re-capture with the new event set
-    c->prof_mask = on & 0xF;
+    const bool serial = (on & CTM_PROFILE_SERIAL) != 0;
+    if ((on & kProfMaskAll) != c->prof_mask || serial != c->prof_serial)
+      drop_graphs(c);  // re-capture with the new event set
+    c->prof_mask = on & kProfMaskAll;
+    c->prof_serial = serial;
   });
 }
 
 int ctm_profile_read(ctm_ctx* c, int cls, long long* launches, double* ms, double* flops) {
-  if (!c || cls < 0 || cls > 3 || !launches || !ms || !flops) return CTM_ERR_ARG;
+  if (!c || cls < 0 || cls >= kProfClasses || !launches || !ms || !flops) return CTM_ERR_ARG;
   return guarded(c, [&] {
     prof_collect(c);
     *launches = c->prof[cls].count;

@@ -104,6 +104,26 @@ int jacobi_batched(cudaStream_t s, double* X, int nrows, int ncols, int nprob, l
 // The stream on which every cooperative launch of this library runs (one per
 // device, created on first use).
 cudaStream_t coop_stream();
+
+// Cooperative launch of fn on that stream, ordered after the work issued so far
+// on s and before the work issued on s later (events).  t0 / t1 (optional) are
+// recorded on the cooperative stream right before and after the kernel.
+cudaError_t launch_cooperative(const void* fn, dim3 grid, dim3 block, void** args, size_t smem,
+                               cudaStream_t s, cudaEvent_t t0 = nullptr,
+                               cudaEvent_t t1 = nullptr);
+
+// ---- fused CholeskyQR (cholqr.cu) ----
+// Q (row-major rows x n) = an orthonormal basis of the columns of Y (row-major
+// rows x n, not modified) by `passes` CholeskyQR passes, the first shifted when
+// `shifted`, in one cooperative launch on the cooperative stream.  work holds
+// cholqr_work_doubles(rows, n) doubles (not zeroed by the caller).  A barrier
+// timeout sets *err_word; floored pivots of the shifted pass add to *floored.
+// n <= 512.  Returns 0, -1 (arguments) or -3 (launch).
+constexpr int kCholqrMaxN = 512;
+size_t cholqr_work_doubles(int rows, int n);
+int cholqr_fused(cudaStream_t s, const double* Y, double* Q, int rows, int n, int passes,
+                 bool shifted, double* work, int* err_word, int* floored, unsigned long long seed,
+                 long long* launches, cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);
 constexpr double kValuesOnlyTol = 1e-10;
 
 // Column norms of X (nrows x ncols col-major) into sig[ncols]; perm[r] = index of

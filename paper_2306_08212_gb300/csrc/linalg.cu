@@ -316,10 +316,26 @@ cudaStream_t coop_stream() {
 
 // Launch fn on the cooperative stream, ordered after the work so far on s and
 // before the work issued later on s.
+// An event record that becomes an event-record node when the stream is being
+// captured into a CUDA graph (so that every replay records it).
+static void record_event(cudaEvent_t ev, cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+  else
+    cudaEventRecord(ev, s);
+}
+
 static cudaError_t launch_coop_ordered(const void* fn, dim3 grid, dim3 block, void** args,
-                                       cudaStream_t s, bool serialize) {
+                                       cudaStream_t s, bool serialize, size_t smem = 0,
+                                       cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr) {
   cudaStream_t cs = serialize ? coop_stream() : nullptr;
-  if (!cs) return cudaLaunchCooperativeKernel(fn, grid, block, args, 0, s);
+  if (!cs) {
+    if (t0) record_event(t0, s);
+    const cudaError_t r = cudaLaunchCooperativeKernel(fn, grid, block, args, smem, s);
+    if (t1) record_event(t1, s);
+    return r;
+  }
   cudaEvent_t e1, e2;
   if (cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) return cudaErrorUnknown;
   if (cudaEventCreateWithFlags(&e2, cudaEventDisableTiming) != cudaSuccess) {
@@ -328,12 +344,21 @@ static cudaError_t launch_coop_ordered(const void* fn, dim3 grid, dim3 block, vo
   }
   cudaError_t e = cudaEventRecord(e1, s);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, e1, 0);
-  if (e == cudaSuccess) e = cudaLaunchCooperativeKernel(fn, grid, block, args, 0, cs);
+  // timing events on the cooperative stream bracket the kernel alone (that
+  // stream runs one cooperative kernel at a time)
+  if (e == cudaSuccess && t0) record_event(t0, cs);
+  if (e == cudaSuccess) e = cudaLaunchCooperativeKernel(fn, grid, block, args, smem, cs);
+  if (e == cudaSuccess && t1) record_event(t1, cs);
   if (e == cudaSuccess) e = cudaEventRecord(e2, cs);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s, e2, 0);
   cudaEventDestroy(e1);
   cudaEventDestroy(e2);
   return e;
+}
+
+cudaError_t launch_cooperative(const void* fn, dim3 grid, dim3 block, void** args, size_t smem,
+                               cudaStream_t s, cudaEvent_t t0, cudaEvent_t t1) {
+  return launch_coop_ordered(fn, grid, block, args, s, true, smem, t0, t1);
 }
 
 int jacobi_onesided(cudaStream_t s, double* X, int nrows, int ncols, double* V, DevFlags* flags,

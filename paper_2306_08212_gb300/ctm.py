@@ -19,6 +19,7 @@ LEFT, UP, RIGHT, DOWN = 0, 1, 2, 3
 STANDARD, REDUCED_SEQUENTIAL, REDUCED_ENV = 0, 1, 2
 FP64, TF32, BF16 = 0, 1, 2
 INIT_NO_GROW = 0x100
+PROFILE_SERIAL = 0x100
 DIRS = {"left": LEFT, "up": UP, "right": RIGHT, "down": DOWN}
 MODES = {"standard": STANDARD, "reduced_sequential": REDUCED_SEQUENTIAL,
          "reduced_env": REDUCED_ENV}
@@ -52,6 +53,7 @@ SIGNATURES = {
                                           ctypes.c_longlong, _D, _D, _D]),
     "ctm_truncated_svd_test": (ctypes.c_int, [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int,
                                                ctypes.c_int, _D]),
+    "ctm_cholqr_test": (ctypes.c_int, [_D, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]),
     "ctm_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int]),
     "ctm_batch_move": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "ctm_batch_last_error": (ctypes.c_char_p, [_P]),
@@ -196,10 +198,11 @@ def ctm_kernel_launches(ctx):
     return load().ctm_kernel_launches(ctx)
 
 
-PROFILE_CLASSES = {0: "gemm_f64", 1: "tc_tf32_gemm", 2: "tc_bf16_gemm", 3: "jacobi_f64"}
+PROFILE_CLASSES = {0: "gemm_f64", 1: "tc_tf32_gemm", 2: "tc_bf16_gemm", 3: "jacobi_f64",
+                   4: "cholqr_f64"}
 
 
-def ctm_profile_enable(ctx, mask=0xF):
+def ctm_profile_enable(ctx, mask=0x1F):
     """Time the kernel classes whose bit (1 << class) is set; 0 stops."""
     return load().ctm_profile_enable(ctx, int(mask))
 
@@ -212,7 +215,7 @@ def ctm_profile_read(ctx, cls):
     return rc, n.value, ms.value, fl.value
 
 
-def ctm_kernel_stats_reset(ctx, mask=0xF):
+def ctm_kernel_stats_reset(ctx, mask=0x1F):
     """Clear and start the per-class CUDA-event kernel timing."""
     rc = ctm_profile_enable(ctx, mask)
     if rc != OK:
@@ -249,6 +252,16 @@ def ctm_truncated_svd_test(path, M, k):
     U = np.zeros((rows, int(k)))
     rc = load().ctm_truncated_svd_test(int(path), _dptr(M), rows, cols, int(k), _dptr(U))
     return rc, U
+
+
+def ctm_cholqr_test(Y, passes):
+    """Orthonormal basis of the columns of the host matrix Y by the library's FP64
+    CholeskyQR (first pass shifted).  Returns (status, Q)."""
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    rows, n = Y.shape
+    Q = np.zeros((rows, n))
+    rc = load().ctm_cholqr_test(_dptr(Y), rows, n, int(passes), _dptr(Q))
+    return rc, Q
 
 
 def ctm_svd_left_adjoint(U, s, Vt, gU, eps=1e-12, stream=None):

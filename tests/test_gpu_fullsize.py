@@ -6,16 +6,20 @@ errors of the mixed-precision modes stated against FP64.
   with a decaying spectrum (the shape of every CTM projector problem), compared as
   subspaces (RMS sine of the principal angles).
 * FP64 reduced-sequential moves with factorisations of n = chi D = 1200 (D=3,
-  chi=400) and n = 2048 (D=8, chi=256, the size of the bench) against the oracle.
-* FP64 standard moves with n = chi D^2 = 1152 and 2160 (the second above the exact
-  limit, so on the randomized path) on environments grown by both sides.
+  chi=400) and n = 2048 (D=8, chi=256, the size of the bench) against the oracle:
+  both above the exact-Jacobi limit (1024), so on the randomized path.
+* FP64 standard moves with n = chi D^2 = 768 (exact Jacobi) and 1280 (randomized)
+  on environments grown from the fold by both sides (D=4).
 * TF32 and BF16 errors against the oracle at D=6, chi=144 and against the FP64 path
   (itself pinned above) at D=8, chi=256 after four iterations.
 
 Gauge-invariant outputs only: the 8 corner spectra, the spectra of the 8 edges
 reshaped as (prev) x (ket, bra, next) and (prev, ket, bra) x (next) (an isometry
 changes an edge only by orthogonal maps on its bond legs), bond energies and ln kappa.
-Inputs: seeded random sites (N(0,1), unit norm) and seeded random environments.
+Inputs: seeded random sites (N(0,1), unit norm) and seeded positive random
+environments (sums of two ket (x) bra products, chi = c0^2): a positive boundary
+keeps ln kappa and the energies physical, and two terms break the Kronecker
+degeneracies of a single product.
 """
 import time
 
@@ -94,9 +98,10 @@ def _decaying(rng, rows, cols, decades):
 
 
 @pytest.mark.parametrize("path,rows,cols,k", [(0, 2500, 2300, 256), (2, 1400, 1300, 200),
-                                              (1, 1400, 1300, 200), (1, 300, 2100, 90)])
+                                              (1, 1400, 1300, 200), (1, 300, 2100, 90),
+                                              (0, 2048, 2048, 256), (2, 3000, 500, 300)])
 def test_truncated_svd_paths_match_lapack(ctm, path, rows, cols, k):
-    """path 0 at min side 2300 > 2048 takes the randomized subspace iteration."""
+    """path 0 above min side 1024 takes the randomized subspace iteration."""
     rng = np.random.default_rng(rows + cols + k)
     M = _decaying(rng, rows, cols, 12)
     rc, U = ctm.ctm_truncated_svd_test(path, M, k)
@@ -124,10 +129,11 @@ def _compare_fp64(g, env, A, B, energies=True, lnk=True):
 
 
 def test_fp64_reduced_sequential_d3_chi400_matches_oracle(ctm):
-    """n = chi D = 1200: above the old exact-Jacobi limit; left then up move."""
-    D, chi = 3, 400
+    """n = chi D = 1200: above the exact-Jacobi limit; left then up move."""
+    D, c0 = 3, 20
+    chi = c0 * c0
     A, B = I.random_sites(2, D, 3)
-    env = I.random_env_tensors(D, chi, seed=2)
+    env = I.positive_env_tensors(D, c0, seed=2)
     g = ctm.Env(A, B, chi, precision=ctm.FP64 | ctm.INIT_NO_GROW)
     try:
         _set_env(g, env)
@@ -143,9 +149,10 @@ def test_fp64_reduced_sequential_d3_chi400_matches_oracle(ctm):
 
 def test_fp64_reduced_sequential_d8_chi256_matches_oracle(ctm):
     """The size of the bench: every v1 factorisation is 2048 x 2048."""
-    D, chi = 8, 256
+    D, c0 = 8, 16
+    chi = c0 * c0
     A, B = I.random_sites(2, D, 0)
-    env = I.random_env_tensors(D, chi, seed=2)
+    env = I.positive_env_tensors(D, c0, seed=2)
     g = ctm.Env(A, B, chi, precision=ctm.FP64 | ctm.INIT_NO_GROW)
     try:
         _set_env(g, env)
@@ -163,11 +170,11 @@ def test_fp64_reduced_sequential_d8_chi256_matches_oracle(ctm):
         g.free()
 
 
-@pytest.mark.parametrize("chi,moves", [(128, ("left", "up", "right", "down")), (240, ("left",))])
+@pytest.mark.parametrize("chi,moves", [(48, ("left", "up", "right", "down")), (80, ("left", "up"))])
 def test_fp64_standard_grown_matches_oracle(ctm, chi, moves):
-    """D=3: the standard projector factorises n = chi D^2 = 1152 (exact Jacobi) and
-    2160 (randomized subspace iteration) on environments grown from the fold."""
-    D = 3
+    """D=4: the standard projector factorises n = chi D^2 = 768 (exact Jacobi) and
+    1280 (randomized subspace iteration) on environments grown from the fold."""
+    D = 4
     A, B = I.random_sites(2, D, 4)
     env = O.init_env(A, B, chi)
     g = ctm.Env(A, B, chi, precision=ctm.FP64)
@@ -177,7 +184,7 @@ def test_fp64_standard_grown_matches_oracle(ctm, chi, moves):
             O.move(env, d, A, B, chi, chi, "standard")
             g.move(d, "standard")
         gaps = _compare_fp64(g, env, A, B)
-        print(f"FP64 standard D=3 chi={chi}: grown {gaps0}, after {len(moves)} moves {gaps}")
+        print(f"FP64 standard D=4 chi={chi}: grown {gaps0}, after {len(moves)} moves {gaps}")
         assert all(v < TOL for v in gaps0.values())
         assert all(v < TOL for v in gaps.values())
     finally:
@@ -199,11 +206,12 @@ def _run(ctm, prec, A, B, chi, env, iters):
 
 
 def test_mixed_precision_errors_vs_oracle_d6_chi144(ctm):
-    """D=6, chi=144 (random sites, seeded random starting environment), two
+    """D=6, chi=144 (random sites, seeded positive starting environment), two
     reduced-sequential iterations: FP64, TF32 and BF16 against the oracle."""
-    D, chi, iters = 6, 144, 2
+    D, c0, iters = 6, 12, 2
+    chi = c0 * c0
     A, B = I.random_sites(2, D, 0)
-    env0 = I.random_env_tensors(D, chi, seed=2)
+    env0 = I.positive_env_tensors(D, c0, seed=2)
     env = {k: v.copy() for k, v in env0.items()}
     for _ in range(iters):
         for d in O.MOVE_ORDER:
@@ -224,11 +232,12 @@ def test_mixed_precision_errors_vs_oracle_d6_chi144(ctm):
 
 
 def test_mixed_precision_errors_vs_fp64_d8_chi256(ctm):
-    """The bench size, four reduced-sequential iterations from one seeded random
+    """The bench size, four reduced-sequential iterations from one seeded positive
     environment in FP64 (pinned to the oracle above), TF32 and BF16."""
-    D, chi, iters = 8, 256, 4
+    D, c0, iters = 8, 16, 4
+    chi = c0 * c0
     A, B = I.random_sites(2, D, 0)
-    env0 = I.random_env_tensors(D, chi, seed=2)
+    env0 = I.positive_env_tensors(D, c0, seed=2)
     res = {}
     for prec in ("fp64", "tf32", "bf16"):
         t0 = time.perf_counter()
