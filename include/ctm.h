@@ -153,6 +153,36 @@ int ctm_get_tensor(ctm_ctx* ctx, int kind, int k, int x, double* out, int* dims)
 int ctm_set_tensor(ctm_ctx* ctx, int kind, int k, int x, const double* in,
                    const int* dims);
 
+/*
+ * Replace the site tensors A and B of a context (same d and D; host or device
+ * pointers, copied; Sec. II) and keep its environment: the next moves and
+ * observables use the new A, B.  Recorded CUDA graphs are discarded and
+ * double-layer tensors already built are rebuilt.
+ */
+int ctm_set_sites(ctm_ctx* ctx, const double* A, const double* B);
+
+/*
+ * Reverse mode (Sec. III-IV and the Appendix, differentiated): the loss
+ *   E = (1/4) sum over the 4 bonds of <op>  (the bond observable of
+ *       ctm_expect_bond, e.g. the Heisenberg S.S of Eq. 1)
+ * evaluated after `iters` iterations (left, up, right, down) of the
+ * reduced-sequential move started from the context's current environment,
+ * which is held fixed (a constant of the loss) and is not modified; and its
+ * gradient with respect to A and B, through every sequential absorption
+ * (Fig. 4b), projector application and truncated SVD (Fig. 4a, Fig. 8).
+ * Everything runs in FP64 on the device, whatever the context's precision: the
+ * truncated SVDs are exact one-sided Jacobi SVDs whose thin factors feed the
+ * adjoint of ctm_svd_left_adjoint with Lorentzian broadening eps (relative to
+ * s_max^4, e.g. 1e-12).  Each iteration is checkpointed: only the environment
+ * entering it is kept, and the backward pass recomputes it.
+ * op: host, (d*d) x (d*d) row-major.  energy: host.  gA, gB: d*D^4 doubles each
+ * (host or device, may be NULL), laid out like A and B.
+ * Errors: CTM_ERR_ARG (iters < 0, eps < 0, null op or energy), CTM_ERR_NAN,
+ * CTM_ERR_NOCONV, CTM_ERR_OOM, CTM_ERR_CUDA.
+ */
+int ctm_energy_grad(ctm_ctx* ctx, int iters, double eps, const double* op, double* energy,
+                    double* gA, double* gB);
+
 /* Number of kernels this library launched on the context so far.
  * (Measurement; no counterpart in the paper.) */
 long long ctm_kernel_launches(ctm_ctx* ctx);

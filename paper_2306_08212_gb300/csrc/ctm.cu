@@ -1641,6 +1641,26 @@ void copy_in(ctm_ctx* c, double* dst, const double* src, size_t n) {
   ck(cudaMemcpyAsync(dst, src, sizeof(double) * n, kind, c->stream), "copy in");
 }
 
+// Rotated copies rot^r(A), rot^r(B), r = 1..3 (a quarter turn each:
+// rot(A)[p, a1, a2, a3, a4] = A[p, a2, a3, a4, a1]).
+void rotate_sites(ctm_ctx* c) {
+  const int d = c->d, D = c->D;
+  LegMap m;
+  const long long D4 = (long long)D * D * D * D, D3 = (long long)D * D * D;
+  push(m, d, D4);
+  push(m, D, 1);
+  push(m, D, D3);
+  push(m, D, (long long)D * D);
+  push(m, D, D);
+  for (int r = 1; r < 4; ++r)
+    for (int x = 0; x < 2; ++x) {
+      ck(permute_f64(c->stream, c->site[r][x], c->site[r - 1][x], m), "rotate");
+      ++c->launches;
+    }
+}
+
+#include "ctm_reverse.cuh"
+
 }  // namespace
 
 // ===========================================================================
@@ -1692,19 +1712,7 @@ int ctm_init_env(ctm_ctx** out, const double* A, const double* B, int d, int D, 
       for (int x = 0; x < 2; ++x) c->site[r][x] = owned_alloc(c, ns);
     copy_in(c, c->site[0][0], A, ns);
     copy_in(c, c->site[0][1], B, ns);
-    // rot(A)[p, a1, a2, a3, a4] = A[p, a2, a3, a4, a1]
-    LegMap m;
-    const long long D4 = (long long)D * D * D * D, D3 = (long long)D * D * D;
-    push(m, d, D4);
-    push(m, D, 1);
-    push(m, D, D3);
-    push(m, D, (long long)D * D);
-    push(m, D, D);
-    for (int r = 1; r < 4; ++r)
-      for (int x = 0; x < 2; ++x) {
-        ck(permute_f64(c->stream, c->site[r][x], c->site[r - 1][x], m), "rotate");
-        ++c->launches;
-      }
+    rotate_sites(c);
     c->bnd = owned_alloc(c, (long long)D * D);
     if (boundary) {
       copy_in(c, c->bnd, boundary, (size_t)D * D);
@@ -1842,6 +1850,46 @@ int ctm_set_tensor(ctm_ctx* c, int kind, int k, int x, const double* in, const i
     ck(cudaMemcpyAsync(t.p, in, sizeof(double) * t.size(), cudaMemcpyHostToDevice, c->stream),
        "h2d");
     ck(cudaStreamSynchronize(c->stream), "sync");
+  });
+}
+
+int ctm_set_sites(ctm_ctx* c, const double* A, const double* B) {
+  if (!c || !A || !B) return CTM_ERR_ARG;
+  return guarded(c, [&] {
+    drop_graphs(c);  // recorded graphs read the old site tensors
+    const long long ns = (long long)c->d * c->D * c->D * c->D * c->D;
+    copy_in(c, c->site[0][0], A, ns);
+    copy_in(c, c->site[0][1], B, ns);
+    rotate_sites(c);
+    // double-layer tensors built so far are rebuilt in place
+    for (int r = 0; r < 4; ++r)
+      for (int x = 0; x < 2; ++x) {
+        if (!c->dbl[r][x]) continue;
+        Ten sx;
+        site(c, r, x, sx);
+        Tmp a = ein64(c, "puldr,pULDR->uUlLdDrR", sx, sx);
+        ck(cudaMemcpyAsync(c->dbl[r][x], a.t.p, sizeof(double) * a.t.size(),
+                           cudaMemcpyDeviceToDevice, c->stream),
+           "dbl");
+      }
+    ck(cudaStreamSynchronize(c->stream), "sync");
+  });
+}
+
+int ctm_energy_grad(ctm_ctx* c, int iters, double eps, const double* op, double* energy,
+                    double* gA, double* gB) {
+  if (!c || iters < 0 || !(eps >= 0.0) || !op || !energy) return CTM_ERR_ARG;
+  return guarded(c, [&] {
+    const long long ns = (long long)c->d * c->D * c->D * c->D * c->D;
+    Tmp ga(c, {(int)ns}), gb(c, {(int)ns});
+    const double E = energy_grad(c, iters, eps, op, ga, gb);
+    if (gA)
+      ck(cudaMemcpyAsync(gA, ga.t.p, sizeof(double) * ns, cudaMemcpyDefault, c->stream), "grad");
+    if (gB)
+      ck(cudaMemcpyAsync(gB, gb.t.p, sizeof(double) * ns, cudaMemcpyDefault, c->stream), "grad");
+    ck(cudaStreamSynchronize(c->stream), "sync");
+    check_flags(c);
+    *energy = E;
   });
 }
 

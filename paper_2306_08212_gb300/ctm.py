@@ -54,6 +54,8 @@ SIGNATURES = {
     "ctm_truncated_svd_test": (ctypes.c_int, [ctypes.c_int, _D, ctypes.c_int, ctypes.c_int,
                                                ctypes.c_int, _D]),
     "ctm_cholqr_test": (ctypes.c_int, [_D, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D]),
+    "ctm_set_sites": (ctypes.c_int, [_P, _P, _P]),
+    "ctm_energy_grad": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, _D, _D, _P, _P]),
     "ctm_batch_create": (ctypes.c_int, [ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.c_int]),
     "ctm_batch_move": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int]),
     "ctm_batch_last_error": (ctypes.c_char_p, [_P]),
@@ -126,6 +128,8 @@ def ctm_init_env(A, B, chi, chi_prime=0, precision=FP64, boundary=None, stream=N
     rc = lib.ctm_init_env(ctypes.byref(ctx), pa, pb, d, D, int(chi), int(chi_prime),
                           int(precision), pbnd, st)
     del ka, kb, kbnd
+    if rc == OK:
+        _site_shape[ctx.value] = (d, D, D, D, D)
     return rc, ctx
 
 
@@ -297,7 +301,33 @@ def ctm_last_error(ctx):
 
 
 def ctm_free(ctx):
+    _site_shape.pop(getattr(ctx, "value", ctx), None)
     load().ctm_free(ctx)
+
+
+def ctm_set_sites(ctx, A, B):
+    pa, ka = _ptr_of(A)
+    pb, kb = _ptr_of(B)
+    rc = load().ctm_set_sites(ctx, pa, pb)
+    del ka, kb
+    return rc
+
+
+def ctm_energy_grad(ctx, iters, op, eps=1e-12):
+    """(status, E, gA, gB): the mean bond expectation of op after `iters`
+    reduced-sequential iterations from the context's environment, and its gradient
+    with respect to the site tensors (host arrays of the sites' shape)."""
+    op = np.ascontiguousarray(op, dtype=np.float64)
+    shape = _site_shape[ctx.value]
+    e = ctypes.c_double(0.0)
+    gA = np.zeros(shape)
+    gB = np.zeros(shape)
+    rc = load().ctm_energy_grad(ctx, int(iters), float(eps), _dptr(op), ctypes.byref(e),
+                                ctypes.c_void_p(gA.ctypes.data), ctypes.c_void_p(gB.ctypes.data))
+    return rc, e.value, gA, gB
+
+
+_site_shape = {}
 
 
 # --- convenience wrapper -----------------------------------------------------
@@ -363,6 +393,15 @@ class Env:
     def set_tensor(self, kind, k, x, arr):
         self._check(ctm_set_tensor(self.ctx, kind, k, x, arr))
 
+    def set_sites(self, A, B):
+        self._check(ctm_set_sites(self.ctx, A, B))
+
+    def energy_grad(self, iters, op, eps=1e-12):
+        """(E, dE/dA, dE/dB): see ctm_energy_grad."""
+        rc, E, gA, gB = ctm_energy_grad(self.ctx, iters, op, eps)
+        self._check(rc)
+        return E, gA, gB
+
     @property
     def launches(self):
         return ctm_kernel_launches(self.ctx)
@@ -410,3 +449,35 @@ class Batch:
             self.free()
         except Exception:
             pass
+
+
+def _energy_function():
+    import torch
+
+    class CTMEnergy(torch.autograd.Function):
+        """E(A, B): the mean bond expectation of op after `iters` checkpointed
+        reduced-sequential iterations from the environment held by `env` (a
+        constant of the loss).  Forward and reverse pass both run in the library
+        (ctm_set_sites, ctm_energy_grad); backward only scales the stored gradient
+        by the incoming one."""
+
+        @staticmethod
+        def forward(ctx, A, B, env, iters, op, eps):
+            env.set_sites(A.detach(), B.detach())
+            E, gA, gB = env.energy_grad(iters, op, eps)
+            ctx.save_for_backward(torch.as_tensor(gA, dtype=A.dtype, device=A.device),
+                                  torch.as_tensor(gB, dtype=B.dtype, device=B.device))
+            return torch.tensor(E, dtype=A.dtype, device=A.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            gA, gB = ctx.saved_tensors
+            return g * gA, g * gB, None, None, None, None
+
+    return CTMEnergy
+
+
+def ctm_energy(A, B, env, iters, op, eps=1e-12):
+    """Differentiable E(A, B) (torch tensors, float64) through the library's
+    reverse pass; `env` is an Env whose environment is the fixed starting point."""
+    return _energy_function().apply(A, B, env, iters, op, eps)
