@@ -44,17 +44,25 @@ constexpr double kNearIdentity = 1e-8;
 constexpr long long kCqBarrierLimit = 4000000000ll;  // clocks (~2 s)
 constexpr int kCqMaxN = kCholqrMaxN;
 
-struct CqArgs {
+constexpr int kCqMaxProb = kCholqrMaxProb;  // independent problems of one launch
+
+// Per-problem pointers (inputs, outputs and this problem's part of the work buffer).
+struct CqProb {
   const double* Y;
   double* Q;
-  int rows, n, passes, shifted;
-  int nchunk, chunk_rows, npairs, T;
   double* part;     // [nchunk][npairs][32 * 32]
   double* G;        // n x n, lower triangle used
   double* Linv;     // [T][32 * 32]
   double* dscale;   // n
   double* emax;     // [passes] max |G' - I| (bits of a non-negative double)
   int* defmask;     // n
+};
+
+struct CqArgs {
+  int nprob;
+  int rows, n, passes, shifted;
+  int nchunk, chunk_rows, npairs, T;
+  CqProb prob[kCqMaxProb];
   DevFlags* fl;     // this launch's own barrier words (inside the work buffer)
   int* err_out;     // sticky error word of the caller (set on a barrier timeout)
   int* floored;
@@ -131,15 +139,18 @@ __device__ __forceinline__ int pair_index(int bi, int bj, int T) {  // bi <= bj
   return bi * T - bi * (bi - 1) / 2 + (bj - bi);
 }
 
-// Phase G: partial Gram tiles.  Thread (ty, tx) of a 16 x 16 layout owns the 2 x 2
-// outputs (2ty + a, 2tx + b) of the 32 x 32 tile.
-__device__ void gram_partials(const CqArgs& a, const double* __restrict__ X) {
+// Phase G: partial Gram tiles of every problem.  Thread (ty, tx) of a 16 x 16
+// layout owns the 2 x 2 outputs (2ty + a, 2tx + b) of the 32 x 32 tile.
+__device__ void gram_partials(const CqArgs& a, int pass) {
   __shared__ double As[kTb][kTb + 1];
   __shared__ double Bs[kTb][kTb + 1];
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
-  const int items = a.npairs * a.nchunk;
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    const int pair = item % a.npairs, chunk = item / a.npairs;
+  const int per = a.npairs * a.nchunk;
+  for (int item = blockIdx.x; item < a.nprob * per; item += gridDim.x) {
+    const CqProb& P = a.prob[item / per];
+    const double* __restrict__ X = pass == 0 ? P.Y : P.Q;
+    const int local = item % per;
+    const int pair = local % a.npairs, chunk = local / a.npairs;
     int bi, bj;
     pair_of(pair, a.T, bi, bj);
     const int r0 = chunk * a.chunk_rows;
@@ -164,7 +175,7 @@ __device__ void gram_partials(const CqArgs& a, const double* __restrict__ X) {
         acc11 = fma(a1, b1, acc11);
       }
     }
-    double* out = a.part + ((long long)chunk * a.npairs + pair) * (kTb * kTb);
+    double* out = P.part + ((long long)chunk * a.npairs + pair) * (kTb * kTb);
     out[(2 * ty) * kTb + 2 * tx] = acc00;
     out[(2 * ty) * kTb + 2 * tx + 1] = acc01;
     out[(2 * ty + 1) * kTb + 2 * tx] = acc10;
@@ -172,7 +183,8 @@ __device__ void gram_partials(const CqArgs& a, const double* __restrict__ X) {
   }
 }
 
-__device__ __forceinline__ double gram_entry(const CqArgs& a, int i, int j) {  // any i, j
+__device__ __forceinline__ double gram_entry(const CqArgs& a, const CqProb& P, int i,
+                                             int j) {  // any i, j
   if (i > j) {
     const int t = i;
     i = j;
@@ -182,38 +194,43 @@ __device__ __forceinline__ double gram_entry(const CqArgs& a, int i, int j) {  /
   const long long off =
       (long long)pair_index(bi, bj, a.T) * (kTb * kTb) + (i % kTb) * kTb + (j % kTb);
   double s = 0.0;
-  for (int c = 0; c < a.nchunk; ++c) s += a.part[(long long)c * a.npairs * (kTb * kTb) + off];
+  for (int c = 0; c < a.nchunk; ++c) s += P.part[(long long)c * a.npairs * (kTb * kTb) + off];
   return s;
 }
 
-// Phase R: G' (lower triangle) = D^-1 G D^-1 + shift I, D, and max |G' - I|.
-__device__ void reduce_scale(const CqArgs& a, double shift, double* emax) {
+// Phase R: G' (lower triangle) = D^-1 G D^-1 + shift I, D, and max |G' - I|, for
+// every problem.
+__device__ void reduce_scale(const CqArgs& a, double shift, int pass) {
   const long long nn = (long long)a.n * a.n;
-  double local = 0.0;
-  for (long long e = blockIdx.x * (long long)kCqThreads + threadIdx.x; e < nn;
-       e += (long long)gridDim.x * kCqThreads) {
-    const int i = (int)(e / a.n), j = (int)(e % a.n);
-    if (j > i) continue;
-    const double gii = gram_entry(a, i, i), gjj = gram_entry(a, j, j);
-    const double di = gii > 0.0 ? sqrt(gii) : 1.0, dj = gjj > 0.0 ? sqrt(gjj) : 1.0;
-    double v = gram_entry(a, i, j) / (di * dj);
-    if (i == j) {
-      v += shift;
-      a.dscale[i] = di;
+  for (int p = 0; p < a.nprob; ++p) {
+    const CqProb& P = a.prob[p];
+    double local = 0.0;
+    for (long long e = blockIdx.x * (long long)kCqThreads + threadIdx.x; e < nn;
+         e += (long long)gridDim.x * kCqThreads) {
+      const int i = (int)(e / a.n), j = (int)(e % a.n);
+      if (j > i) continue;
+      const double gii = gram_entry(a, P, i, i), gjj = gram_entry(a, P, j, j);
+      const double di = gii > 0.0 ? sqrt(gii) : 1.0, dj = gjj > 0.0 ? sqrt(gjj) : 1.0;
+      double v = gram_entry(a, P, i, j) / (di * dj);
+      if (i == j) {
+        v += shift;
+        P.dscale[i] = di;
+      }
+      P.G[(long long)i * a.n + j] = v;
+      local = fmax(local, fabs(v - (i == j ? 1.0 : 0.0)));
     }
-    a.G[(long long)i * a.n + j] = v;
-    local = fmax(local, fabs(v - (i == j ? 1.0 : 0.0)));
+    for (int o = 16; o > 0; o >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, o));
+    if ((threadIdx.x & 31) == 0 && local > 0.0)
+      atomicMax(reinterpret_cast<unsigned long long*>(P.emax + pass),
+                (unsigned long long)__double_as_longlong(local));
   }
-  for (int o = 16; o > 0; o >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, o));
-  if ((threadIdx.x & 31) == 0 && local > 0.0)
-    atomicMax(reinterpret_cast<unsigned long long*>(emax),
-              (unsigned long long)__double_as_longlong(local));
 }
 
 // Diagonal block p: Cholesky in place (lower) and its inverse into Linv[p], on
 // warp 0 of the calling block.  Pivot rules: shifted pass -> floor at `floor`
 // (counted); unshifted passes -> a pivot <= tau marks a dependent column.
-__device__ void diag_factor(const CqArgs& a, int p, double floor, double tau, bool use_mask) {
+__device__ void diag_factor(const CqArgs& a, const CqProb& P, int p, double floor, double tau,
+                            bool use_mask) {
   __shared__ double L[kTb][kTb + 1];
   __shared__ double X[kTb][kTb + 1];
   __shared__ double rinv[kTb];
@@ -221,7 +238,7 @@ __device__ void diag_factor(const CqArgs& a, int p, double floor, double tau, bo
   const int j0 = p * kTb, jb = min(kTb, a.n - j0);
   if (threadIdx.x < 32) {
     for (int j = 0; j < kTb; ++j)
-      L[lane][j] = (lane < jb && j < jb && j <= lane) ? a.G[(long long)(j0 + lane) * a.n + j0 + j]
+      L[lane][j] = (lane < jb && j < jb && j <= lane) ? P.G[(long long)(j0 + lane) * a.n + j0 + j]
                                                       : 0.0;
     __syncwarp();
     for (int k = 0; k < jb; ++k) {
@@ -239,7 +256,7 @@ __device__ void diag_factor(const CqArgs& a, int p, double floor, double tau, bo
       if (lane == k) {
         L[k][k] = piv;
         rinv[k] = 1.0 / piv;
-        if (dep) a.defmask[j0 + k] = 1;
+        if (dep) P.defmask[j0 + k] = 1;
         if (floored) atomicAdd(a.floored, 1);
       }
       if (lane > k && lane < jb) L[lane][k] = dep ? 0.0 : L[lane][k] / piv;
@@ -262,29 +279,33 @@ __device__ void diag_factor(const CqArgs& a, int p, double floor, double tau, bo
       __syncwarp();
     }
     for (int i = 0; i < kTb; ++i) {
-      if (i < jb && lane < jb) a.G[(long long)(j0 + i) * a.n + j0 + lane] = lane <= i ? L[i][lane] : 0.0;
-      a.Linv[(long long)p * kTb * kTb + i * kTb + lane] = X[i][lane];
+      if (i < jb && lane < jb) P.G[(long long)(j0 + i) * a.n + j0 + lane] = lane <= i ? L[i][lane] : 0.0;
+      P.Linv[(long long)p * kTb * kTb + i * kTb + lane] = X[i][lane];
     }
   }
 }
 
-// Panel p: L_ip = G'_ip Linv_pp^T for block rows i > p; items are 8-row groups.
-__device__ void panel_solve(const CqArgs& a, int p) {
+// Panel p: L_ip = G'_ip Linv_pp^T for block rows i > p of every problem that
+// takes the Cholesky (chol[q]); items are 8-row groups.
+__device__ void panel_solve(const CqArgs& a, int p, const bool* chol) {
   __shared__ double Li[kTb][kTb + 1];
   __shared__ double Gr[8][kTb + 1];
   const int tid = threadIdx.x;
   const int j0 = p * kTb, jb = min(kTb, a.n - j0);
   const int r_lo = j0 + jb;
   const int groups = (a.n - r_lo + 7) / 8;
-  for (int item = blockIdx.x; item < groups; item += gridDim.x) {
-    const int r0 = r_lo + item * 8;
+  for (int item = blockIdx.x; item < a.nprob * groups; item += gridDim.x) {
+    const int q = item / groups;
+    if (!chol[q]) continue;
+    const CqProb& P = a.prob[q];
+    const int r0 = r_lo + (item % groups) * 8;
     __syncthreads();
     for (int e = tid; e < kTb * kTb; e += kCqThreads)
-      Li[e / kTb][e % kTb] = a.Linv[(long long)p * kTb * kTb + e];
+      Li[e / kTb][e % kTb] = P.Linv[(long long)p * kTb * kTb + e];
     {
       const int rr = tid / kTb, cc = tid % kTb;
       const int r = r0 + rr;
-      Gr[rr][cc] = (r < a.n && cc < jb) ? a.G[(long long)r * a.n + j0 + cc] : 0.0;
+      Gr[rr][cc] = (r < a.n && cc < jb) ? P.G[(long long)r * a.n + j0 + cc] : 0.0;
     }
     __syncthreads();
     const int rr = tid / kTb, cc = tid % kTb;
@@ -292,22 +313,26 @@ __device__ void panel_solve(const CqArgs& a, int p) {
 #pragma unroll 8
     for (int k = 0; k < kTb; ++k) acc = fma(Gr[rr][k], Li[cc][k], acc);
     const int r = r0 + rr;
-    if (r < a.n && cc < jb) a.G[(long long)r * a.n + j0 + cc] = acc;
+    if (r < a.n && cc < jb) P.G[(long long)r * a.n + j0 + cc] = acc;
   }
 }
 
 // Trailing update after panel p: G'_ij -= L_ip L_jp^T for p < bj <= bi (block
-// coordinates), lower blocks only; items are (block pair, 8-row group).
-__device__ void trailing_update(const CqArgs& a, int p) {
+// coordinates), lower blocks only; items are (problem, block pair, 8-row group).
+__device__ void trailing_update(const CqArgs& a, int p, const bool* chol) {
   __shared__ double Lj[kTb][kTb + 1];
   __shared__ double Lr[8][kTb + 1];
   const int tid = threadIdx.x;
   const int j0 = p * kTb, jb = min(kTb, a.n - j0);
   const int nb = a.T - p - 1;  // remaining block rows/cols
   const int pairs = nb * (nb + 1) / 2;
-  const int items = pairs * 4;
-  for (int item = blockIdx.x; item < items; item += gridDim.x) {
-    const int pr = item / 4, g = item % 4;
+  const int per = pairs * 4;
+  for (int item = blockIdx.x; item < a.nprob * per; item += gridDim.x) {
+    const int q = item / per;
+    if (!chol[q]) continue;
+    const CqProb& P = a.prob[q];
+    const int local = item % per;
+    const int pr = local / 4, g = local % 4;
     int ci, cj;  // ci <= cj in 0..nb-1 : block col = p+1+ci, block row = p+1+cj
     pair_of(pr, nb, ci, cj);
     const int bc = p + 1 + ci, br = p + 1 + cj;
@@ -316,12 +341,12 @@ __device__ void trailing_update(const CqArgs& a, int p) {
     for (int e = tid; e < kTb * kTb; e += kCqThreads) {
       const int rr = e / kTb, kk = e % kTb;
       const int r = bc * kTb + rr;
-      Lj[rr][kk] = (r < a.n && kk < jb) ? a.G[(long long)r * a.n + j0 + kk] : 0.0;
+      Lj[rr][kk] = (r < a.n && kk < jb) ? P.G[(long long)r * a.n + j0 + kk] : 0.0;
     }
     {
       const int rr = tid / kTb, kk = tid % kTb;
       const int r = r0 + rr;
-      Lr[rr][kk] = (r < a.n && kk < jb) ? a.G[(long long)r * a.n + j0 + kk] : 0.0;
+      Lr[rr][kk] = (r < a.n && kk < jb) ? P.G[(long long)r * a.n + j0 + kk] : 0.0;
     }
     __syncthreads();
     const int rr = tid / kTb, cc = tid % kTb;
@@ -330,15 +355,15 @@ __device__ void trailing_update(const CqArgs& a, int p) {
       double acc = 0.0;
 #pragma unroll 8
       for (int k = 0; k < kTb; ++k) acc = fma(Lr[rr][k], Lj[cc][k], acc);
-      a.G[(long long)r * a.n + col] -= acc;
+      P.G[(long long)r * a.n + col] -= acc;
     }
   }
 }
 
 // Phase T: Q = X D^-1 L^-T (full) or Q = X D^-1 (I - U) (near identity) for the
 // 16-row blocks this CTA owns; then, when asked, flagged columns become Gaussian.
-__device__ void substitute(const CqArgs& a, const double* __restrict__ X, bool near_id,
-                           bool refill, unsigned long long seed) {
+__device__ void substitute(const CqArgs& a, int pass, const bool* near_ids, const bool* refills,
+                           unsigned long long seed) {
   extern __shared__ double dyn[];
   double* Xs = dyn;                      // [kRowBlock][n] scaled input rows
   double* Qs = dyn + kRowBlock * a.n;    // [kRowBlock][n] output rows
@@ -346,13 +371,17 @@ __device__ void substitute(const CqArgs& a, const double* __restrict__ X, bool n
   __shared__ double Tt[kRowBlock][kTb + 1];
   const int tid = threadIdx.x;
   const int nblk = (a.rows + kRowBlock - 1) / kRowBlock;
-  for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-    const int r0 = blk * kRowBlock;
+  for (int item = blockIdx.x; item < a.nprob * nblk; item += gridDim.x) {
+    const int q = item / nblk;
+    const CqProb& P = a.prob[q];
+    const double* __restrict__ X = pass == 0 ? P.Y : P.Q;
+    const bool near_id = near_ids[q], refill = refills[q];
+    const int r0 = (item % nblk) * kRowBlock;
     __syncthreads();
     for (int e = tid; e < kRowBlock * a.n; e += kCqThreads) {
       const int rr = e / a.n, cc = e % a.n;
       const int r = r0 + rr;
-      Xs[e] = r < a.rows ? X[(long long)r * a.n + cc] / a.dscale[cc] : 0.0;
+      Xs[e] = r < a.rows ? X[(long long)r * a.n + cc] / P.dscale[cc] : 0.0;
     }
     __syncthreads();
     for (int p = 0; p < a.T; ++p) {
@@ -365,7 +394,7 @@ __device__ void substitute(const CqArgs& a, const double* __restrict__ X, bool n
         __syncthreads();
         for (int e = tid; e < kTb * kTb; e += kCqThreads) {
           const int i = e / kTb, k = e % kTb;  // Lt[i][k] = L[j0 + i][k0 + k]
-          Lt[i][k] = (i < jb) ? a.G[(long long)(j0 + i) * a.n + k0 + k] : 0.0;
+          Lt[i][k] = (i < jb) ? P.G[(long long)(j0 + i) * a.n + k0 + k] : 0.0;
         }
         __syncthreads();
 #pragma unroll 8
@@ -380,7 +409,7 @@ __device__ void substitute(const CqArgs& a, const double* __restrict__ X, bool n
         __syncthreads();
         for (int e = tid; e < kTb * kTb; e += kCqThreads) {
           const int i = e / kTb, k = e % kTb;
-          Lt[i][k] = (i < jb && k < i) ? a.G[(long long)(j0 + i) * a.n + j0 + k] : 0.0;
+          Lt[i][k] = (i < jb && k < i) ? P.G[(long long)(j0 + i) * a.n + j0 + k] : 0.0;
         }
         __syncthreads();
         for (int k = 0; k < kTb; ++k) {
@@ -398,7 +427,7 @@ __device__ void substitute(const CqArgs& a, const double* __restrict__ X, bool n
         Tt[rr0 + 8][cc] = cc < jb ? Xs[(rr0 + 8) * a.n + j0 + cc] - acc1 : 0.0;
         __syncthreads();
         for (int e = tid; e < kTb * kTb; e += kCqThreads)
-          Lt[e / kTb][e % kTb] = a.Linv[(long long)p * kTb * kTb + e];
+          Lt[e / kTb][e % kTb] = P.Linv[(long long)p * kTb * kTb + e];
         __syncthreads();
         double q0 = 0.0, q1 = 0.0;
 #pragma unroll 8
@@ -419,9 +448,9 @@ __device__ void substitute(const CqArgs& a, const double* __restrict__ X, bool n
       const int r = r0 + rr;
       if (r >= a.rows) continue;
       double v = Qs[e];
-      if (refill && a.defmask[cc])
+      if (refill && P.defmask[cc])
         v = cq_gauss(seed, (unsigned long long)cc * a.rows + r);
-      a.Q[(long long)r * a.n + cc] = v;
+      P.Q[(long long)r * a.n + cc] = v;
     }
   }
 }
@@ -435,46 +464,51 @@ __global__ void __launch_bounds__(kCqThreads, 1) cholqr_kernel(CqArgs a) {
 }
 
 __device__ bool cholqr_passes(const CqArgs& a, double u) {
+  __shared__ bool s_chol[kCqMaxProb], s_near[kCqMaxProb], s_refill[kCqMaxProb];
   for (int pass = 0; pass < a.passes; ++pass) {
-    const double* X = pass == 0 ? a.Y : a.Q;
     const bool shift_pass = pass == 0 && a.shifted;
-    gram_partials(a, X);
+    gram_partials(a, pass);
     if (!cq_barrier(a.fl)) return false;
-    // the mask of the previous pass has been read by every block by now
-    for (int j = blockIdx.x * kCqThreads + threadIdx.x; j < a.n; j += gridDim.x * kCqThreads)
-      a.defmask[j] = 0;
+    // the masks of the previous pass have been read by every block by now
+    for (int q = 0; q < a.nprob; ++q)
+      for (int j = blockIdx.x * kCqThreads + threadIdx.x; j < a.n; j += gridDim.x * kCqThreads)
+        a.prob[q].defmask[j] = 0;
     const double shift =
         shift_pass ? 11.0 * ((double)a.rows * a.n + (double)a.n * (a.n + 1)) * u * a.n : 0.0;
-    reduce_scale(a, shift, a.emax + pass);
+    reduce_scale(a, shift, pass);
     if (!cq_barrier(a.fl)) return false;
-    // every block must take the same branch (the barrier count depends on it):
-    // thread 0 reads the reduced maximum with an acquire load and broadcasts it
-    __shared__ double s_e;
+    // every block must take the same branches (the barrier count depends on them):
+    // thread 0 reads each reduced maximum with an acquire load and broadcasts it
     if (threadIdx.x == 0) {
-      unsigned long long bits;
-      asm volatile("ld.acquire.gpu.global.u64 %0, [%1];"
-                   : "=l"(bits)
-                   : "l"(a.emax + pass)
-                   : "memory");
-      s_e = __longlong_as_double((long long)bits);
+      for (int q = 0; q < a.nprob; ++q) {
+        unsigned long long bits;
+        asm volatile("ld.acquire.gpu.global.u64 %0, [%1];"
+                     : "=l"(bits)
+                     : "l"(a.prob[q].emax + pass)
+                     : "memory");
+        const double e = __longlong_as_double((long long)bits);
+        s_near[q] = !shift_pass && e < kNearIdentity;
+        s_chol[q] = !s_near[q];
+        s_refill[q] = !s_near[q] && pass > 0 && pass + 1 < a.passes;
+      }
     }
     __syncthreads();
-    const double e = s_e;
-    const bool near_id = !shift_pass && e < kNearIdentity;
-    if (!near_id) {
+    bool any_chol = false;
+    for (int q = 0; q < a.nprob; ++q) any_chol = any_chol || s_chol[q];
+    if (any_chol) {
       for (int p = 0; p < a.T; ++p) {
-        if (blockIdx.x == 0) diag_factor(a, p, 1e-28, 1e-12, !shift_pass && pass > 0);
+        if (blockIdx.x < a.nprob && s_chol[blockIdx.x])
+          diag_factor(a, a.prob[blockIdx.x], p, 1e-28, 1e-12, !shift_pass && pass > 0);
         if (!cq_barrier(a.fl)) return false;
-        panel_solve(a, p);
+        panel_solve(a, p, s_chol);
         if (!cq_barrier(a.fl)) return false;
         if (p + 1 < a.T) {
-          trailing_update(a, p);
+          trailing_update(a, p, s_chol);
           if (!cq_barrier(a.fl)) return false;
         }
       }
     }
-    const bool refill = !near_id && pass > 0 && pass + 1 < a.passes;
-    substitute(a, X, near_id, refill, a.seed + (unsigned long long)pass);
+    substitute(a, pass, s_near, s_refill, a.seed + (unsigned long long)pass);
     if (!cq_barrier(a.fl)) return false;
   }
   return true;
@@ -503,42 +537,55 @@ int cholqr_sm_count() {
 
 }  // namespace
 
-size_t cholqr_work_doubles(int rows, int n) {
+// doubles of one problem's part of the work buffer
+size_t cholqr_prob_doubles(int rows, int n) {
   const int nsm = cholqr_sm_count();
   int T, npairs, nchunk, chunk_rows;
   cholqr_layout(rows, n, nsm > 0 ? nsm : 1, T, npairs, nchunk, chunk_rows);
   return (size_t)nchunk * npairs * kTb * kTb + (size_t)n * n + (size_t)T * kTb * kTb + n + 8 +
-         (size_t)(n + 1) / 2 + 8;
+         (size_t)(n + 1) / 2;
 }
 
-int cholqr_fused(cudaStream_t s, const double* Y, double* Q, int rows, int n, int passes,
-                 bool shifted, double* work, int* err_word, int* floored, unsigned long long seed,
-                 long long* launches, cudaEvent_t t0, cudaEvent_t t1) {
-  if (n < 1 || n > kCqMaxN || rows < 1 || passes < 1 || passes > 8) return -1;
+size_t cholqr_work_doubles(int rows, int n, int nprob) {
+  return (size_t)nprob * cholqr_prob_doubles(rows, n) + 8;
+}
+
+int cholqr_fused_batch(cudaStream_t s, int nprob, const double* const* Y, double* const* Q,
+                       int rows, int n, int passes, bool shifted, double* work, int* err_word,
+                       int* floored, unsigned long long seed, long long* launches, cudaEvent_t t0,
+                       cudaEvent_t t1) {
+  if (nprob < 1 || nprob > kCqMaxProb || n < 1 || n > kCqMaxN || rows < 1 || passes < 1 ||
+      passes > 8)
+    return -1;
   const int nsm = cholqr_sm_count();
   if (nsm < 1) return -3;
   CqArgs a;
-  a.Y = Y;
-  a.Q = Q;
+  a.nprob = nprob;
   a.rows = rows;
   a.n = n;
   a.passes = passes;
   a.shifted = shifted ? 1 : 0;
   cholqr_layout(rows, n, nsm, a.T, a.npairs, a.nchunk, a.chunk_rows);
-  double* w = work;
-  a.part = w;
-  w += (size_t)a.nchunk * a.npairs * kTb * kTb;
-  a.G = w;
-  w += (size_t)n * n;
-  a.Linv = w;
-  w += (size_t)a.T * kTb * kTb;
-  a.dscale = w;
-  w += n;
-  a.emax = w;
-  w += 8;
-  a.defmask = reinterpret_cast<int*>(w);
-  w += (n + 1) / 2;
-  a.fl = reinterpret_cast<DevFlags*>(w);
+  const size_t per = cholqr_prob_doubles(rows, n);
+  for (int q = 0; q < nprob; ++q) {
+    CqProb& P = a.prob[q];
+    P.Y = Y[q];
+    P.Q = Q[q];
+    double* w = work + (size_t)q * per;
+    P.part = w;
+    w += (size_t)a.nchunk * a.npairs * kTb * kTb;
+    P.G = w;
+    w += (size_t)n * n;
+    P.Linv = w;
+    w += (size_t)a.T * kTb * kTb;
+    P.dscale = w;
+    w += n;
+    P.emax = w;
+    w += 8;
+    P.defmask = reinterpret_cast<int*>(w);
+    if (cudaMemsetAsync(P.emax, 0, 8 * sizeof(double), s) != cudaSuccess) return -3;
+  }
+  a.fl = reinterpret_cast<DevFlags*>(work + (size_t)nprob * per);
   static_assert(sizeof(DevFlags) <= 8 * sizeof(double), "DevFlags must fit its slot");
   a.err_out = err_word;
   a.floored = floored;
@@ -558,8 +605,7 @@ int cholqr_fused(cudaStream_t s, const double* Y, double* Q, int rows, int n, in
           cudaSuccess ||
       per_sm < 1)
     return -3;
-  // this launch's barrier words and per-pass maxima start at zero
-  if (cudaMemsetAsync(a.emax, 0, 8 * sizeof(double), s) != cudaSuccess) return -3;
+  // this launch's barrier words start at zero
   if (cudaMemsetAsync(a.fl, 0, sizeof(DevFlags), s) != cudaSuccess) return -3;
   void* args[] = {&a};
   if (launch_cooperative(reinterpret_cast<const void*>(cholqr_kernel), dim3(nsm),
@@ -567,6 +613,13 @@ int cholqr_fused(cudaStream_t s, const double* Y, double* Q, int rows, int n, in
     return -3;
   ++*launches;
   return 0;
+}
+
+int cholqr_fused(cudaStream_t s, const double* Y, double* Q, int rows, int n, int passes,
+                 bool shifted, double* work, int* err_word, int* floored, unsigned long long seed,
+                 long long* launches, cudaEvent_t t0, cudaEvent_t t1) {
+  return cholqr_fused_batch(s, 1, &Y, &Q, rows, n, passes, shifted, work, err_word, floored, seed,
+                            launches, t0, t1);
 }
 
 }  // namespace ctm

@@ -456,7 +456,8 @@ Tmp sorted_unit_columns(ctm_ctx* c, double* X, int nrows, int ncols, int k) {
 // moving, with a Jacobi SVD of the projected problem.  path: 0 = that choice,
 // 1 = exact, 2 = randomized (test hook).
 enum SvdPath { kSvdAuto = 0, kSvdExact = 1, kSvdRandomized = 2 };
-Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k, int path = kSvdAuto);
+Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k, int path = kSvdAuto,
+                  int slot = -1);
 
 
 // CTM_TRACE=1 prints every factorisation (shape, path, time, Jacobi sweeps of
@@ -470,14 +471,14 @@ bool trace_on() {
   return on == 1;
 }
 
-Tmp left_svd(ctm_ctx* c, const double* M, int rows, int cols, int k) {
-  if (!trace_on()) return left_svd_impl(c, M, rows, cols, k);
+Tmp left_svd(ctm_ctx* c, const double* M, int rows, int cols, int k, int slot = -1) {
+  if (!trace_on()) return left_svd_impl(c, M, rows, cols, k, kSvdAuto, slot);
   ck(cudaStreamSynchronize(c->stream), "sync");
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, c->stream);
-  Tmp U = left_svd_impl(c, M, rows, cols, k);
+  Tmp U = left_svd_impl(c, M, rows, cols, k, kSvdAuto, slot);
   cudaEventRecord(e1, c->stream);
   ck(cudaStreamSynchronize(c->stream), "sync");
   float ms = 0.f;
@@ -500,9 +501,9 @@ double subspace_change(ctm_ctx* c, const double* Uold, const double* Unew, int r
 
 // Randomized subspace iteration run to convergence (defined with the
 // CholeskyQR it orthonormalises with).
-Tmp left_svd_subspace(ctm_ctx* c, const double* M, int rows, int cols, int k);
+Tmp left_svd_subspace(ctm_ctx* c, const double* M, int rows, int cols, int k, int slot);
 
-Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k, int path) {
+Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k, int path, int slot) {
   if (k >= rows) return identity(c, rows);
   if (k > std::min(rows, cols)) fail(CTM_ERR_ARG, "truncation rank exceeds the matrix rank bound");
   const bool exact = path == kSvdExact || (path == kSvdAuto && std::min(rows, cols) <= kExactSvdMax);
@@ -534,7 +535,7 @@ Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k, int pa
     dfree(c, perm);
     return U;
   }
-  return left_svd_subspace(c, M, rows, cols, k);
+  return left_svd_subspace(c, M, rows, cols, k, slot);
 }
 
 double subspace_change(ctm_ctx* c, const double* Uold, const double* Unew, int rows, int ld,
@@ -718,7 +719,7 @@ Tmp cholqr_chain(ctm_ctx* c, const double* Y, long long ys_r, long long ys_c, in
 // Ritz vectors no longer moves (RMS principal-angle sine < kSubspaceTol, or
 // stagnation at the rounding floor) or after kMaxPowerIters; inside a stream
 // capture the host cannot look, so kCapturedPowerIters sweeps run.
-Tmp left_svd_subspace(ctm_ctx* c, const double* M, int rows, int cols, int k) {
+Tmp left_svd_subspace(ctm_ctx* c, const double* M, int rows, int cols, int k, int slot) {
   const int l = std::min(k + std::max(kMinOversample, k / 2), std::min(rows, cols));
   // Y = M X with X row-major cols x l: Y row-major rows x l
   auto times_M = [&](const double* X) {
@@ -740,6 +741,15 @@ Tmp left_svd_subspace(ctm_ctx* c, const double* M, int rows, int cols, int k) {
     ck(gaussian_fill(c->stream, Om.t.p, (long long)cols * l, c->seed++), "gaussian");
     ++c->launches;
     Tmp Y = times_M(Om.t.p);
+    // warm start: the leading k columns start from the converged basis of the
+    // previous call at this position (the oversampling columns stay random)
+    if (slot >= 0) {
+      const auto& ce = c->cache[slot];
+      if (ce.p && ce.rows == rows && ce.k == k)
+        ck(cudaMemcpy2DAsync(Y.t.p, sizeof(double) * l, ce.p, sizeof(double) * k,
+                             sizeof(double) * k, rows, cudaMemcpyDeviceToDevice, c->stream),
+           "warm start");
+    }
     Q = cholqr(c, Y.t.p, l, 1, rows, l, 3);
   }
   const int max_iters = c->capturing ? kCapturedPowerIters : kMaxPowerIters;
@@ -778,6 +788,17 @@ Tmp left_svd_subspace(ctm_ctx* c, const double* M, int rows, int cols, int k) {
     if (it + 1 == max_iters) break;
     Tmp Y = times_M(Qz.t.p);
     Q = cholqr(c, Y.t.p, l, 1, rows, l, 3);
+  }
+  if (slot >= 0 && !c->capturing) {  // keep the converged basis for the next call here
+    auto& ce = c->cache[slot];
+    if (!ce.p || ce.rows != rows || ce.k != k) {
+      ce.p = owned_alloc(c, (long long)rows * k);
+      ce.rows = rows;
+      ce.k = k;
+    }
+    ck(cudaMemcpyAsync(ce.p, Uk.t.p, sizeof(double) * rows * k, cudaMemcpyDeviceToDevice,
+                       c->stream),
+       "cache");
   }
   return Uk;
 }
@@ -826,6 +847,103 @@ Tmp left_svd_power(ctm_ctx* c, const double* M, int rows, int cols, int k, int s
   ck(cudaMemcpyAsync(ce.p, Q.t.p, sizeof(double) * rows * k, cudaMemcpyDeviceToDevice, c->stream),
      "cache");
   return Q;
+}
+
+// Orthonormal bases of nprob same-shape row-major matrices Y[q] (rows x n) by
+// `passes` CholeskyQR passes (the first shifted), in one fused cooperative
+// launch: the problems share its barriers and Cholesky latency.
+void cholqr_batch(ctm_ctx* c, int nprob, const double* const* Y, Tmp* Q, int rows, int n,
+                  int passes) {
+  if (n > kCholqrMaxN || rows < n || nprob > kCholqrMaxProb) {
+    for (int q = 0; q < nprob; ++q) Q[q] = cholqr(c, Y[q], n, 1, rows, n, passes);
+    return;
+  }
+  double* qp[kCholqrMaxProb];
+  for (int q = 0; q < nprob; ++q) {
+    Q[q] = Tmp(c, {rows, n});
+    qp[q] = Q[q].t.p;
+  }
+  Tmp W(c, {(int)cholqr_work_doubles(rows, n, nprob)});
+  {
+    const double flops =
+        nprob * passes * (2.0 * rows * n * (double)n + (double)n * n * n / 3.0);
+    ProfScope ps(c, 4, flops, true);
+    const int rc = cholqr_fused_batch(c->stream, nprob, Y, qp, rows, n, passes, true, W.t.p,
+                                      &c->flags->error, c->floored, c->seed, &c->launches,
+                                      ps.ev0(), ps.ev1());
+    c->seed += passes;
+    if (rc != 0) fail(CTM_ERR_CUDA, "fused CholeskyQR launch failed");
+  }
+  for (int q = 0; q < nprob; ++q) check_finite(c, Q[q].t, "cholqr");
+}
+
+// left_svd_power for nprob matrices of one shape in lockstep (slot[q] per
+// problem): the tensor-core products per problem, every orthonormalisation as
+// one batched CholeskyQR.  Problems without a cached basis start from a
+// Gaussian sketch; the sweep count is the largest any problem needs.
+void left_svd_power_batch(ctm_ctx* c, int nprob, const double* const* M, int rows, int cols,
+                          int k, const int* slot, Tmp* Q) {
+  bool warm[kCholqrMaxProb];
+  int iters = 0;
+  bool any_cold = false;
+  for (int q = 0; q < nprob; ++q) {
+    auto& ce = c->cache[slot[q]];
+    warm[q] = ce.p && ce.rows == rows && ce.k == k;
+    iters = std::max(iters, warm[q] ? kWarmIters : kColdIters);
+    any_cold = any_cold || !warm[q];
+  }
+  if (any_cold) {
+    Tmp Y[kCholqrMaxProb];
+    const double* yp[kCholqrMaxProb];
+    for (int q = 0; q < nprob; ++q) {
+      Y[q] = Tmp(c, {rows, k});
+      if (warm[q]) {
+        ck(cudaMemcpyAsync(Y[q].t.p, c->cache[slot[q]].p, sizeof(double) * rows * k,
+                           cudaMemcpyDeviceToDevice, c->stream),
+           "cache");
+      } else {
+        Tmp Om(c, {cols, k});
+        ck(gaussian_fill(c->stream, Om.t.p, (long long)cols * k, c->seed++), "gaussian");
+        ++c->launches;
+        gemm_mixed(c, rows, k, cols, M[q], lm1(rows, cols), lm1(cols, 1), Om.t.p, lm1(cols, k),
+                   lm1(k, 1), Y[q].t.p, lm1(rows, k), lm1(k, 1));
+      }
+      yp[q] = Y[q].t.p;
+    }
+    cholqr_batch(c, nprob, yp, Q, rows, k, 4);
+  } else {
+    for (int q = 0; q < nprob; ++q) {
+      Q[q] = Tmp(c, {rows, k});
+      ck(cudaMemcpyAsync(Q[q].t.p, c->cache[slot[q]].p, sizeof(double) * rows * k,
+                         cudaMemcpyDeviceToDevice, c->stream),
+         "cache");
+    }
+  }
+  for (int it = 0; it < iters; ++it) {
+    Tmp Y[kCholqrMaxProb];
+    const double* yp[kCholqrMaxProb];
+    for (int q = 0; q < nprob; ++q) {
+      Tmp Z(c, {cols, k});
+      gemm_mixed(c, cols, k, rows, M[q], lm1(cols, 1), lm1(rows, cols), Q[q].t.p, lm1(rows, k),
+                 lm1(k, 1), Z.t.p, lm1(cols, k), lm1(k, 1));
+      Y[q] = Tmp(c, {rows, k});
+      gemm_mixed(c, rows, k, cols, M[q], lm1(rows, cols), lm1(cols, 1), Z.t.p, lm1(cols, k),
+                 lm1(k, 1), Y[q].t.p, lm1(rows, k), lm1(k, 1));
+      yp[q] = Y[q].t.p;
+    }
+    cholqr_batch(c, nprob, yp, Q, rows, k, 3);
+  }
+  for (int q = 0; q < nprob; ++q) {
+    auto& ce = c->cache[slot[q]];
+    if (!ce.p || ce.rows != rows || ce.k != k) {
+      ce.p = owned_alloc(c, (long long)rows * k);
+      ce.rows = rows;
+      ce.k = k;
+    }
+    ck(cudaMemcpyAsync(ce.p, Q[q].t.p, sizeof(double) * rows * k, cudaMemcpyDeviceToDevice,
+                       c->stream),
+       "cache");
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -949,7 +1067,7 @@ Proj projector_standard(ctm_ctx* c, int r, int x) {
                     k <= cols;
   // mixed precision: subspace iteration (cache slots 48.. for the standard projectors)
   Tmp U = fast ? left_svd_power(c, Q.t.p, rows, cols, k, 48 + r * 2 + x)
-               : left_svd(c, Q.t.p, rows, cols, k);
+               : left_svd(c, Q.t.p, rows, cols, k, 48 + r * 2 + x);
   P.v = std::move(U);
   P.v.t = view(P.v.t, {na, D, D, k});
   return P;
@@ -982,7 +1100,7 @@ Proj projector_reduced_env(ctm_ctx* c, int r, int x) {
                     k <= cols;
   Proj P;
   Tmp U = fast ? left_svd_power(c, Q.t.p, rows, cols, k, 56 + r * 2 + x)
-               : left_svd(c, Q.t.p, rows, cols, k);
+               : left_svd(c, Q.t.p, rows, cols, k, 56 + r * 2 + x);
   P.v = std::move(U);
   P.v.t = view(P.v.t, {na, D, D, k});
   return P;
@@ -997,7 +1115,7 @@ void split_projector(ctm_ctx* c, const Ten& Mt, Tmp& v1, Tmp& v2, Tmp& N, int sl
   if (fast && k1 < na * D && k1 <= D * nb)
     v1 = left_svd_power(c, Mt.p, na * D, D * nb, k1, slot);
   else
-    v1 = left_svd(c, Mt.p, na * D, D * nb, k1);
+    v1 = left_svd(c, Mt.p, na * D, D * nb, k1, slot);
   v1.t = view(v1.t, {na, D, k1});
   N = ein(c, "akc,akbz->cbz", v1, Mt);
   const int k2 = std::min(c->chi, k1 * D);
@@ -1006,6 +1124,37 @@ void split_projector(ctm_ctx* c, const Ten& Mt, Tmp& v1, Tmp& v2, Tmp& N, int sl
   else
     v2 = left_svd(c, N.t.p, k1 * D, nb, k2);
   v2.t = view(v2.t, {k1, D, k2});
+}
+
+// split_projector for nprob networks of one shape at once (mixed precision):
+// the subspace iterations in lockstep, each orthonormalisation batched.
+void split_projector_batch(ctm_ctx* c, int nprob, const Ten* Mt, Tmp* v1, Tmp* v2, Tmp* N,
+                           const int* slot) {
+  const int na = Mt[0].dims[0], D = Mt[0].dims[1], nb = Mt[0].dims[3];
+  bool same = true;
+  for (int q = 1; q < nprob; ++q)
+    for (int i = 0; i < 4; ++i) same = same && Mt[q].dims[i] == Mt[0].dims[i];
+  const int k1 = std::min(c->chip, na * D);
+  if (!same || c->precision == CTM_FP64 || !(k1 < na * D && k1 <= D * nb)) {
+    for (int q = 0; q < nprob; ++q) split_projector(c, Mt[q], v1[q], v2[q], N[q], slot[q]);
+    return;
+  }
+  const double* mp[kCholqrMaxProb];
+  for (int q = 0; q < nprob; ++q) mp[q] = Mt[q].p;
+  left_svd_power_batch(c, nprob, mp, na * D, D * nb, k1, slot, v1);
+  for (int q = 0; q < nprob; ++q) {
+    v1[q].t = view(v1[q].t, {na, D, k1});
+    N[q] = ein(c, "akc,akbz->cbz", v1[q], Mt[q]);
+  }
+  const int k2 = std::min(c->chi, k1 * D);
+  if (k2 == nb && k2 < k1 * D) {  // the whole column space: any orthonormal basis
+    const double* np[kCholqrMaxProb];
+    for (int q = 0; q < nprob; ++q) np[q] = N[q].t.p;
+    cholqr_batch(c, nprob, np, v2, k1 * D, nb, 3);
+  } else {
+    for (int q = 0; q < nprob; ++q) v2[q] = left_svd(c, N[q].t.p, k1 * D, nb, k2);
+  }
+  for (int q = 0; q < nprob; ++q) v2[q].t = view(v2[q].t, {k1, D, k2});
 }
 
 // Sequential ket-then-bra absorption of an edge T[prev, k, b, next] with the
@@ -1079,12 +1228,58 @@ Proj projector_seq(ctm_ctx* c, int r, int x, int col) {
   return P;
 }
 
+// Both reduced-network projectors of a column (Sec. III-IV, Fig. 3c, Fig. 8) in
+// the mixed-precision path: the four boundary factorisations (v_l, v_r of both
+// sublattices) share their orthonormalisations, then the two reduced networks do.
+void projectors_seq_batched(ctm_ctx* c, int r, int col, Proj* P) {
+  Ten S[2];
+  Tmp L[2], R[2];
+  int base[2];
+  for (int x = 0; x < 2; ++x) {
+    site(c, r, x, S[x]);
+    base[x] = ((r * 2 + col) * 2 + x) * 3;
+    L[x] = ein(c, "dg,akbd->gkba", E(c, 0, 1, x, r), E(c, 1, 1, x, r));
+    R[x] = ein(c, "ez,zkbw->ekbw", E(c, 0, 2, x, r), E(c, 1, 3, x, r));
+  }
+  Tmp Mx[2];
+  {
+    const Ten mats[4] = {L[0].t, R[0].t, L[1].t, R[1].t};
+    const int slots[4] = {base[0] + 0, base[0] + 1, base[1] + 0, base[1] + 1};
+    Tmp v1[4], v2[4], N[4];
+    split_projector_batch(c, 4, mats, v1, v2, N, slots);
+    for (int x = 0; x < 2; ++x) {
+      L[x].release();
+      R[x].release();
+    }
+    for (int x = 0; x < 2; ++x) {
+      const int l = 2 * x, rr = 2 * x + 1;
+      Tmp C1p = ein(c, "cby,cba->ya", v2[l], N[l]);
+      Tmp C2p = ein(c, "cby,cbw->yw", v2[rr], N[rr]);
+      Tmp T2p = absorb_edge_seq(c, E(c, 1, 2, x, r), S[x], "ipon", v1[l], v2[l], v1[rr], v2[rr]);
+      Tmp Xm = ein(c, "ya,ykbz->akbz", C1p, T2p);
+      T2p.release();
+      Mx[x] = ein(c, "akbz,zw->akbw", Xm, C2p);
+    }
+  }
+  const Ten mm[2] = {Mx[0].t, Mx[1].t};
+  const int slots[2] = {base[0] + 2, base[1] + 2};
+  Tmp v1[2], v2[2], N[2];
+  split_projector_batch(c, 2, mm, v1, v2, N, slots);
+  for (int x = 0; x < 2; ++x) {
+    P[x].v1 = std::move(v1[x]);
+    P[x].v2 = std::move(v2[x]);
+  }
+}
+
 // One column absorption in frame r (Sec. II, Fig. 2a-b).
 void column_absorb(ctm_ctx* c, int r, int mode, int col) {
   Proj P[2];
   const cudaStream_t main = c->stream;
-  const bool fork = mode == CTM_REDUCED_SEQUENTIAL && can_fork(c);
-  if (fork) {
+  const bool batched = mode == CTM_REDUCED_SEQUENTIAL && c->precision != CTM_FP64;
+  const bool fork = !batched && mode == CTM_REDUCED_SEQUENTIAL && can_fork(c);
+  if (batched) {
+    projectors_seq_batched(c, r, col, P);
+  } else if (fork) {
     // the two projectors are independent: P_b on side stream 1
     stream_dep(c, main, c->side[1]);
     P[0] = projector_seq(c, r, 0, col);

@@ -120,7 +120,14 @@ cudaError_t launch_cooperative(const void* fn, dim3 grid, dim3 block, void** arg
 // timeout sets *err_word; floored pivots of the shifted pass add to *floored.
 // n <= 512.  Returns 0, -1 (arguments) or -3 (launch).
 constexpr int kCholqrMaxN = 512;
-size_t cholqr_work_doubles(int rows, int n);
+constexpr int kCholqrMaxProb = 4;
+size_t cholqr_work_doubles(int rows, int n, int nprob = 1);
+// nprob (<= kCholqrMaxProb) independent problems of the same shape in one launch:
+// they share the barriers and the latency-bound Cholesky steps.
+int cholqr_fused_batch(cudaStream_t s, int nprob, const double* const* Y, double* const* Q,
+                       int rows, int n, int passes, bool shifted, double* work, int* err_word,
+                       int* floored, unsigned long long seed, long long* launches,
+                       cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);
 int cholqr_fused(cudaStream_t s, const double* Y, double* Q, int rows, int n, int passes,
                  bool shifted, double* work, int* err_word, int* floored, unsigned long long seed,
                  long long* launches, cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);

@@ -299,6 +299,13 @@ int t_trunc(Tape& T, int M, int rows, int cols, int k) {
     ++c->launches;
   }
   const bool kst = T.konst[M];
+  // When Jacobi runs on M's columns, a column of X whose singular value is
+  // (numerically) zero normalises to noise, not to a direction orthogonal to
+  // the others; the adjoint needs U to be an orthonormal basis (its columns for
+  // zero values span the complement).  CholeskyQR keeps the span of every
+  // leading set of columns, so it leaves the nonzero-value columns as they are
+  // (to rounding) and completes the rest orthonormally.
+  if (u_from_x && !kst) U = cholqr(c, U.t.p, r, 1, rows, r, 3);
   const int out = T.own(std::move(Uk), kst);
   if (!kst) {
     ROp op;

@@ -72,23 +72,25 @@ def random_env_tensors(D, chi, seed=0):
     return env
 
 
-def positive_env_tensors(D, c0, seed=0, terms=2):
+def positive_env_tensors(D, c0, seed=0, terms=2, decay=0.0):
     """Random environment at bond dimension chi = c0^2 whose every tensor is a sum of
     `terms` ket (x) bra products (C = sum_t c_t (x) c_t, T = sum_t t_t (x) t_t, the
     boundary legs fused ket-slow), so that it is a positive boundary: every norm and
     density matrix it closes is a sum of squares, and energies lie in the spectrum of
     the operator.  With terms >= 2 the spectra carry no exact degeneracies of the
-    Kronecker kind.  c_t, t_t ~ N(0, 1); each sum scaled to unit norm.  Keyed
-    ('C' | 'T', k, 'a' | 'b')."""
+    Kronecker kind.  c_t, t_t ~ N(0, 1), their bond legs weighted by exp(-decay i)
+    (index i of the leg; decay > 0 gives decaying spectra, like those of a converged
+    environment); each sum scaled to unit norm.  Keyed ('C' | 'T', k, 'a' | 'b')."""
     rng = np.random.default_rng(seed)
+    w = np.exp(-decay * np.arange(c0))
     env = {}
     for k in range(1, 5):
         for x in "ab":
             C = np.zeros((c0 * c0, c0 * c0))
             T = np.zeros((c0 * c0, D, D, c0 * c0))
             for _ in range(terms):
-                c = rng.standard_normal((c0, c0))
-                t = rng.standard_normal((c0, D, c0))
+                c = rng.standard_normal((c0, c0)) * w[:, None] * w[None, :]
+                t = rng.standard_normal((c0, D, c0)) * w[:, None, None] * w[None, None, :]
                 C += np.einsum("ab,AB->aAbB", c, c).reshape(c0 * c0, c0 * c0)
                 T += np.einsum("akb,AKB->aAkKbB", t, t).reshape(c0 * c0, D, D, c0 * c0)
             env[("C", k, x)] = _unit(C)
