@@ -89,6 +89,7 @@ __device__ __forceinline__ void block_sum3(double& a, double& b, double& c) {
 }
 
 constexpr int kJacobiThreads = 256;
+constexpr int kWarpJacobiMaxRows = 4096;  // warp-per-pair Jacobi up to this column length
 
 // Column held at round-robin position p during step s (n even, position 0 fixed).
 __device__ __forceinline__ int rr_col(int p, int s, int n) {
@@ -193,7 +194,8 @@ jacobi_kernel(double* __restrict__ Xall, int nrows, int ncols, int npad, double*
 // overlaps within a step.  Same rotation, ordering and stopping rule.
 __global__ void __launch_bounds__(kJacobiThreads)
 jacobi_warp_kernel(double* __restrict__ Xall, int nrows, int ncols, int npad, DevFlags* fl,
-                   int max_sweeps, double tol, int nprob, long long pstride, double tiny_rel) {
+                   int max_sweeps, double tol, int nprob, long long pstride, double tiny_rel,
+                   double* __restrict__ V) {
   const unsigned nblocks = gridDim.x;
   const int npairs = npad / 2;
   const int lane = threadIdx.x % 32;
@@ -246,6 +248,15 @@ jacobi_warp_kernel(double* __restrict__ Xall, int nrows, int ncols, int npad, De
           const double u = xi[r], v = xj[r];
           xi[r] = c * u - sn * v;
           xj[r] = sn * u + c * v;
+        }
+        if (V) {  // one problem only when the rotations are accumulated
+          double* vi = V + (long long)i * ncols;
+          double* vj = V + (long long)j * ncols;
+          for (int r = lane; r < ncols; r += 32) {
+            const double u = vi[r], v = vj[r];
+            vi[r] = c * u - sn * v;
+            vj[r] = sn * u + c * v;
+          }
         }
       }
       if (!grid_barrier(fl, nblocks)) return;
@@ -381,13 +392,26 @@ int jacobi_onesided(cudaStream_t s, double* X, int nrows, int ncols, double* V, 
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, jacobi_kernel, kJacobiThreads, 0);
   if (per_sm < 1) return -3;
-  int grid = npad / 2;
-  if (grid > nsm) grid = nsm;  // one block per SM: fewer arrivals per barrier
   if (cudaMemsetAsync(flags, 0, kDevFlagsResetBytes, s) != cudaSuccess) return -3;
   const double tol = 2.220446049250313e-16 * std::sqrt((double)(nrows > 1 ? nrows : 1));
   int nprob = 1;
   long long pstride = 0;
   double tiny_rel = 1e-32;
+  if (nrows <= kWarpJacobiMaxRows) {
+    // one warp per column pair (eight per block): the FP64 latency of several
+    // pairs overlaps; same rotation, ordering and stopping rule
+    long long want = ((long long)(npad / 2) + kJacobiThreads / 32 - 1) / (kJacobiThreads / 32);
+    const int wgrid = (int)(want < (long long)nsm ? want : (long long)nsm);
+    void* wargs[] = {&X, &nrows, &ncols, (void*)&npad, &flags, &max_sweeps, (void*)&tol,
+                     &nprob, &pstride, &tiny_rel, &V};
+    if (launch_coop_ordered((void*)jacobi_warp_kernel, dim3(wgrid), dim3(kJacobiThreads), wargs,
+                            s, true) != cudaSuccess)
+      return -3;
+    ++*launches;
+    return 0;
+  }
+  int grid = npad / 2;
+  if (grid > nsm) grid = nsm;  // one block per SM: fewer arrivals per barrier
   void* args[] = {&X, &nrows, &ncols, (void*)&npad, &V, &flags, &max_sweeps, (void*)&tol,
                   &nprob, &pstride, &tiny_rel};
   if (launch_coop_ordered((void*)jacobi_kernel, dim3(grid), dim3(kJacobiThreads), args, s, true) !=
@@ -422,7 +446,7 @@ int jacobi_batched(cudaStream_t s, double* X, int nrows, int ncols, int nprob, l
   double tiny_rel = warp_mode ? 1e-24 : 1e-32;
   if (warp_mode) {
     void* wargs[] = {&X, &nrows, &ncols, (void*)&npad, &flags, &max_sweeps, (void*)&tol,
-                     &nprob, &pstride, &tiny_rel};
+                     &nprob, &pstride, &tiny_rel, &V};
     if (launch_coop_ordered((void*)jacobi_warp_kernel, dim3(grid), dim3(kJacobiThreads), wargs, s,
                             serialize) != cudaSuccess)
       return -3;

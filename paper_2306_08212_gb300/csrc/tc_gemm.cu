@@ -16,7 +16,10 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <cstdlib>
+#include <map>
 #include <mutex>
+#include <vector>
 
 #include "tc_gemm.h"
 
@@ -175,11 +178,14 @@ __host__ __device__ constexpr size_t tc_smem_bytes() {
          (2 * tc_stages<BN>() + 2) * 8 + (size_t)BN * 8;
 }
 
+// grid (N tiles, M tiles, splits): split z takes k-tiles [z kps, min((z+1) kps, num_k_tiles)).
+// ws == nullptr: the tile is written as FP64 through the output leg maps; else split z
+// writes its FP32 partial tile to ws[z][m][n] (M x N dense) for splitk_reduce_kernel.
 template <int BN, bool TF32>
 __global__ void __launch_bounds__(128, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                int M, int N, int num_k_tiles, double* __restrict__ C, LegMap Cm, LegMap Cn,
-               int* err) {
+               int* err, int kps, float* __restrict__ ws) {
   constexpr int STAGES = tc_stages<BN>();
   constexpr uint32_t A_BYTES = kBM * kStageKBytes, B_BYTES = BN * kStageKBytes;
   constexpr int KE = TF32 ? 32 : 64;  // elements of K per stage
@@ -198,6 +204,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int n0 = blockIdx.x * BN;
   const int m0 = blockIdx.y * kBM;
+  const int kt_begin = blockIdx.z * kps;
+  const int nkt = min(num_k_tiles - kt_begin, kps);  // >= 1 by construction of the grid
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -229,19 +237,19 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   if (warp == 0 && lane == 0) {
     // producer: TMA
     int kt = 0;
-    for (; kt < num_k_tiles; ++kt) {
+    for (; kt < nkt; ++kt) {
       const int s = kt % STAGES;
       const uint32_t it = kt / STAGES;
       if (!mbar_wait(&empty[s], (it & 1u) ^ 1u, err)) break;
       mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
-      tma_load_2d(sA + s * A_BYTES, &mapA, &full[s], kt * KE, m0);
-      tma_load_2d(sB + s * B_BYTES, &mapB, &full[s], kt * KE, n0);
+      tma_load_2d(sA + s * A_BYTES, &mapA, &full[s], (kt_begin + kt) * KE, m0);
+      tma_load_2d(sB + s * B_BYTES, &mapB, &full[s], (kt_begin + kt) * KE, n0);
     }
     s_issued = kt;
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
     int kt = 0;
-    for (; kt < num_k_tiles; ++kt) {
+    for (; kt < nkt; ++kt) {
       const int s = kt % STAGES;
       const uint32_t it = kt / STAGES;
       if (!mbar_wait(&full[s], it & 1u, err)) break;
@@ -271,9 +279,16 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
       uint32_t r[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)j0, r);
       if (m < M) {
+        if (ws) {
+          float* row = ws + ((long long)blockIdx.z * M + m) * N;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          if (n0 + j0 + i < N) C[offm + offCn[j0 + i]] = (double)__uint_as_float(r[i]);
+          for (int i = 0; i < 32; ++i)
+            if (n0 + j0 + i < N) row[n0 + j0 + i] = __uint_as_float(r[i]);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            if (n0 + j0 + i < N) C[offm + offCn[j0 + i]] = (double)__uint_as_float(r[i]);
+          }
         }
       }
     }
@@ -291,6 +306,21 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"((uint32_t)BN));
+  }
+}
+
+// C(m, n) = sum over splits of ws[z][m][n] (in FP64, split order fixed), written
+// through the output leg maps.
+__global__ void splitk_reduce_f32_kernel(const float* __restrict__ ws, int splits, long long M,
+                                         long long N, double* __restrict__ C, LegMap Cm,
+                                         LegMap Cn) {
+  const long long MN = M * N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < MN;
+       i += (long long)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int z = 0; z < splits; ++z) v += (double)ws[z * MN + i];
+    const long long m = i / N, n = i - m * N;
+    C[tc_map_offset(Cm, m) + tc_map_offset(Cn, n)] = v;
   }
 }
 
@@ -404,7 +434,8 @@ bool make_map(TcGemm* t, CUtensorMap* map, void* base, bool tf32, long long rows
 
 template <int BN, bool TF32>
 cudaError_t launch(cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
-                   int nk, double* C, const LegMap& Cm, const LegMap& Cn, int* err) {
+                   int nk, double* C, const LegMap& Cm, const LegMap& Cn, int* err, int splits,
+                   float* ws) {
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
@@ -413,10 +444,20 @@ cudaError_t launch(cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb,
                                     (int)tc_smem_bytes<BN>());
   });
   if (attr_err != cudaSuccess) return attr_err;
-  dim3 grid((N + BN - 1) / BN, (M + kBM - 1) / kBM);
-  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
-  tc_gemm_kernel<BN, TF32><<<grid, 128, tc_smem_bytes<BN>(), s>>>(ma, mb, M, N, nk, C, Cm, Cn, err);
-  return cudaGetLastError();
+  const int kps = (nk + splits - 1) / splits;
+  splits = (nk + kps - 1) / kps;  // every split gets at least one k-tile
+  dim3 grid((N + BN - 1) / BN, (M + kBM - 1) / kBM, splits);
+  if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
+  tc_gemm_kernel<BN, TF32><<<grid, 128, tc_smem_bytes<BN>(), s>>>(ma, mb, M, N, nk, C, Cm, Cn, err,
+                                                                 kps, splits > 1 ? ws : nullptr);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && splits > 1) {
+    long long blocks = ((long long)M * N + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    splitk_reduce_f32_kernel<<<(unsigned)blocks, 256, 0, s>>>(ws, splits, M, N, C, Cm, Cn);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 template <bool TF32>
@@ -426,6 +467,82 @@ cudaError_t pack(cudaStream_t s, void* out, const double* in, const LegMap& Rm, 
   if (gy > 65535 || gx > (1ll << 31) - 1) return cudaErrorInvalidConfiguration;
   pack_kernel<TF32><<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(out, in, Rm, Rk, R, K, Kp);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Tile autotuner: for every contraction shape (M, N, K, precision) met outside a
+// stream capture, the candidate launches (BN in {64, 128, 256}; one K split, or
+// as many splits as bring the tile count near two waves of the SMs) are timed
+// with CUDA events on the contraction's own operands (two runs each, the second
+// counted) and the fastest is kept, process-wide per device, so every context
+// and every later (or captured) launch of that shape uses the same choice.
+// Inside a capture, a shape not yet tuned takes the rule-of-thumb choice.
+// CTM_TC_AUTOTUNE=0 keeps the rule-of-thumb choice everywhere.
+// ---------------------------------------------------------------------------
+struct TcChoice {
+  int bn = 128;
+  int splits = 1;
+};
+
+namespace {
+
+struct TcKey {
+  int dev;
+  long long M, N, K;
+  int tf32;
+  bool operator<(const TcKey& o) const {
+    if (dev != o.dev) return dev < o.dev;
+    if (M != o.M) return M < o.M;
+    if (N != o.N) return N < o.N;
+    if (K != o.K) return K < o.K;
+    return tf32 < o.tf32;
+  }
+};
+
+std::mutex g_tune_mu;
+std::map<TcKey, TcChoice> g_tune;
+
+bool autotune_on() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = std::getenv("CTM_TC_AUTOTUNE");
+    on = (e && *e == '0') ? 0 : 1;
+  }
+  return on == 1;
+}
+
+long long tiles_of(long long M, long long N, int bn) {
+  return ((N + bn - 1) / bn) * ((M + kBM - 1) / kBM);
+}
+
+int pow2_floor(long long v) {
+  int p = 1;
+  while ((long long)p * 2 <= v) p *= 2;
+  return p;
+}
+
+// The K split that brings `tiles` near two waves of 152 SMs, at least two
+// k-tiles per split, at most 16 splits.
+int split_for(long long tiles, int nk) {
+  if (tiles >= 152 || nk < 4) return 1;
+  long long want = (2 * 152 + tiles - 1) / tiles;
+  if (want > nk / 2) want = nk / 2;
+  if (want > 16) want = 16;
+  return want < 2 ? 1 : pow2_floor(want);
+}
+
+TcChoice rule_of_thumb(long long M, long long N, int nk) {
+  TcChoice c;
+  c.bn = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
+  c.splits = split_for(tiles_of(M, N, c.bn), nk);
+  return c;
+}
+
+bool capturing(cudaStream_t s) {
+  cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+  return cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive;
 }
 
 }  // namespace
@@ -442,6 +559,7 @@ int tc_contract(TcGemm* t, cudaStream_t s, int precision, long long M, long long
   const bool tf32 = precision == 1;
   const int esz = tf32 ? 4 : 2;
   const long long Kp = ((K + 7) / 8) * 8;  // 16-byte row pitch
+  const int nk = (int)((Kp + (tf32 ? 32 : 64) - 1) / (tf32 ? 32 : 64));
   void* pa = nullptr;
   void* pb = nullptr;
   if (cudaMallocAsync(&pa, (size_t)(M * Kp * esz), s) != cudaSuccess ||
@@ -454,33 +572,99 @@ int tc_contract(TcGemm* t, cudaStream_t s, int precision, long long M, long long
   if (e == cudaSuccess)
     e = tf32 ? pack<true>(s, pb, B, Bn, Bk, N, K, Kp) : pack<false>(s, pb, B, Bn, Bk, N, K, Kp);
   *launches += 2;
-  const int BN = N <= 64 ? 64 : (N <= 128 ? 128 : 256);
-  CUtensorMap ma, mb;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const TcKey key{dev, M, N, K, tf32 ? 1 : 0};
+  TcChoice choice = rule_of_thumb(M, N, nk);
+  bool known = false;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      choice = it->second;
+      known = true;
+    }
+  }
+  const bool tune = !known && autotune_on() && !capturing(s) && e == cudaSuccess;
+  std::vector<TcChoice> cands;
+  if (tune) {
+    for (int bn : {64, 128, 256}) {
+      TcChoice c;
+      c.bn = bn;
+      c.splits = 1;
+      cands.push_back(c);
+      const int sp = split_for(tiles_of(M, N, bn), nk);
+      if (sp > 1) {
+        c.splits = sp;
+        cands.push_back(c);
+      }
+    }
+  }
+  int max_splits = choice.splits;
+  for (const auto& c : cands) max_splits = std::max(max_splits, c.splits);
+  float* ws = nullptr;
+  if (max_splits > 1 && cudaMallocAsync(&ws, sizeof(float) * (size_t)max_splits * M * N, s) !=
+                            cudaSuccess) {
+    cudaGetLastError();
+    ws = nullptr;
+    choice.splits = 1;
+    for (auto& c : cands) c.splits = 1;
+  }
+  CUtensorMap ma;
   int rc = 0;
-  if (e != cudaSuccess) {
-    rc = -3;
-  } else if (!make_map(t, &ma, pa, tf32, M, Kp, kBM) || !make_map(t, &mb, pb, tf32, N, Kp, BN)) {
+  auto run = [&](const TcChoice& c) -> cudaError_t {
+    CUtensorMap mb;
+    if (!make_map(t, &mb, pb, tf32, N, Kp, c.bn)) return cudaErrorInvalidValue;
+    if (tf32) {
+      return c.bn == 64    ? launch<64, true>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err, c.splits, ws)
+             : c.bn == 128 ? launch<128, true>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err, c.splits, ws)
+                           : launch<256, true>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err, c.splits, ws);
+    }
+    return c.bn == 64    ? launch<64, false>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err, c.splits, ws)
+           : c.bn == 128 ? launch<128, false>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err, c.splits, ws)
+                         : launch<256, false>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err, c.splits, ws);
+  };
+  if (e != cudaSuccess || !make_map(t, &ma, pa, tf32, M, Kp, kBM)) {
     rc = -3;
   } else {
-    const int nk = (int)((Kp + (tf32 ? 32 : 64) - 1) / (tf32 ? 32 : 64));
-    if (ev_begin) record(ev_begin, s);
-    if (tf32) {
-      e = BN == 64    ? launch<64, true>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err)
-          : BN == 128 ? launch<128, true>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err)
-                      : launch<256, true>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err);
-    } else {
-      e = BN == 64    ? launch<64, false>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err)
-          : BN == 128 ? launch<128, false>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err)
-                      : launch<256, false>(s, ma, mb, (int)M, (int)N, nk, C, Cm, Cn, err);
+    if (tune && cands.size() > 1) {
+      cudaEvent_t t0, t1;
+      if (cudaEventCreate(&t0) == cudaSuccess && cudaEventCreate(&t1) == cudaSuccess) {
+        float best = 1e30f;
+        for (const auto& c : cands) {
+          float ms = 1e30f;
+          for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(t0, s);
+            if (run(c) != cudaSuccess) break;
+            cudaEventRecord(t1, s);
+            if (cudaEventSynchronize(t1) != cudaSuccess || cudaEventElapsedTime(&ms, t0, t1) != cudaSuccess)
+              ms = 1e30f;
+          }
+          if (ms < best) {
+            best = ms;
+            choice = c;
+          }
+        }
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
+      }
+      cudaGetLastError();
     }
+    if (tune) {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tune[key] = choice;
+    }
+    if (ev_begin) record(ev_begin, s);
+    e = run(choice);  // the result the caller gets (the last launch on C)
     if (ev_end) record(ev_end, s);
-    ++*launches;
+    *launches += choice.splits > 1 ? 2 : 1;
     if (e != cudaSuccess) rc = -3;
   }
   if (rc != 0 && ev_begin && ev_end) {  // keep the event pair well-formed
     record(ev_begin, s);
     record(ev_end, s);
   }
+  if (ws) cudaFreeAsync(ws, s);
   cudaFreeAsync(pa, s);
   cudaFreeAsync(pb, s);
   return rc;
