@@ -404,7 +404,12 @@ def tensor_core_util(breakdown, ms_per_step, peaks):
 # workload, valid only for the kernel source it was taken on: each entry names the source
 # file and the first 16 hex digits of its SHA-256 at capture time; when the file has changed
 # since, the bench reports traffic null.
-TRAFFIC_PER_LAUNCH = {}
+# cholqr_f64: 17.5 MB read + written per launch of four 2048 x 256 problems (ncu, D=8 chi=256
+# step); the step's launches carry four problems (v1 and v2 of the boundary factorisations)
+# or two (the reduced networks) in equal numbers, and the traffic is the inputs read once,
+# so it scales with the problem count: 3/4 of the four-problem figure per launch on average.
+TRAFFIC_PER_LAUNCH = {"cholqr_f64": ("paper_2306_08212_gb300/csrc/cholqr.cu", "ad6c55a2a189c45c",
+                                     17.50e6 * 3.0 / 4.0)}
 
 
 def measured_traffic(name):
