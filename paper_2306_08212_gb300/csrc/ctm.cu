@@ -753,39 +753,57 @@ Tmp left_svd_subspace(ctm_ctx* c, const double* M, int rows, int cols, int k, in
     Q = cholqr(c, Y.t.p, l, 1, rows, l, 3);
   }
   const int max_iters = c->capturing ? kCapturedPowerIters : kMaxPowerIters;
+  // The Rayleigh-Ritz step (an l x l Jacobi) runs on sweep 0, sweep 1 and then
+  // only where the geometric rate of the subspace movement measured so far says
+  // the span should have converged; the cheap part of a sweep (two products and
+  // two CholeskyQRs) runs every time.
   double prev_moved = INFINITY;
+  int prev_check = -1, next_check = 0;
   Tmp Uk;
   for (int it = 0; it < max_iters; ++it) {
     Tmp Z = times_Mt(Q.t.p);
     Tmp Qz = cholqr(c, Z.t.p, l, 1, cols, l, 3);
-    // R = Qz^T Z (l x l), stored column-major for Jacobi on its columns
-    Tmp Rc(c, {l, l});
-    gemm64(c, l, l, cols, 1.0, Qz.t.p, lm1(l, 1), lm1(cols, l), Z.t.p, lm1(cols, l), lm1(l, 1),
-           0.0, Rc.t.p, lm1(l, 1), lm1(l, l));
-    Z.release();
-    Tmp V(c, {l, l});
-    jacobi(c, Rc.t.p, l, l, V.t.p);
-    Tmp Vk;
-    {
-      Tmp sig(c, {l});
-      int* perm = (int*)dalloc(c, (l + 1) / 2 + 1);
-      ck(column_norms_sorted(c->stream, Rc.t.p, l, l, sig.t.p, perm), "norms");
-      Vk = Tmp(c, {l, k});
-      ck(gather_sorted_columns(c->stream, Vk.t.p, l, k, nullptr, V.t.p, sig.t.p, perm), "gather");
-      c->launches += 3;
-      dfree(c, perm);
+    const bool last = it + 1 == max_iters;
+    if (it == next_check || last) {
+      // R = Qz^T Z (l x l), stored column-major for Jacobi on its columns
+      Tmp Rc(c, {l, l});
+      gemm64(c, l, l, cols, 1.0, Qz.t.p, lm1(l, 1), lm1(cols, l), Z.t.p, lm1(cols, l),
+             lm1(l, 1), 0.0, Rc.t.p, lm1(l, 1), lm1(l, l));
+      Z.release();
+      Tmp V(c, {l, l});
+      jacobi(c, Rc.t.p, l, l, V.t.p);
+      Tmp Vk;
+      {
+        Tmp sig(c, {l});
+        int* perm = (int*)dalloc(c, (l + 1) / 2 + 1);
+        ck(column_norms_sorted(c->stream, Rc.t.p, l, l, sig.t.p, perm), "norms");
+        Vk = Tmp(c, {l, k});
+        ck(gather_sorted_columns(c->stream, Vk.t.p, l, k, nullptr, V.t.p, sig.t.p, perm),
+           "gather");
+        c->launches += 3;
+        dfree(c, perm);
+      }
+      Tmp Un = ein64(c, "ic,cr->ir", Q.t, Vk.t);
+      const bool check = !c->capturing && prev_check >= 0;
+      const double moved = check ? subspace_change(c, Uk.t.p, Un.t.p, rows, k, k) : 1.0;
+      Uk = std::move(Un);
+      if (trace_on() && check)
+        std::fprintf(stderr, "[ctm] subspace iteration %dx%d k=%d l=%d sweep %d: moved %.3e\n",
+                     rows, cols, k, l, it + 1, moved);
+      // converged, or down at the rounding floor (no longer shrinking)
+      if (moved < kSubspaceTol || (moved < 1e-10 && moved > 0.9 * prev_moved)) break;
+      if (last) break;
+      next_check = it + 1;
+      if (check && std::isfinite(prev_moved) && moved < prev_moved) {
+        const double rate = std::pow(moved / prev_moved, 1.0 / (it - prev_check));
+        if (rate < 0.9) {
+          const double sweeps = std::log(kSubspaceTol / moved) / std::log(rate);
+          next_check = it + std::max(1, std::min(8, (int)std::ceil(sweeps)));
+        }
+      }
+      prev_moved = check ? moved : INFINITY;
+      prev_check = it;
     }
-    Tmp Un = ein64(c, "ic,cr->ir", Q.t, Vk.t);
-    const bool check = !c->capturing && it > 0;
-    const double moved = check ? subspace_change(c, Uk.t.p, Un.t.p, rows, k, k) : 1.0;
-    Uk = std::move(Un);
-    if (trace_on() && check)
-      std::fprintf(stderr, "[ctm] subspace iteration %dx%d k=%d l=%d sweep %d: moved %.3e\n",
-                   rows, cols, k, l, it + 1, moved);
-    // converged, or down at the rounding floor (no longer shrinking)
-    if (moved < kSubspaceTol || (moved < 1e-10 && moved > 0.9 * prev_moved)) break;
-    prev_moved = moved;
-    if (it + 1 == max_iters) break;
     Tmp Y = times_M(Qz.t.p);
     Q = cholqr(c, Y.t.p, l, 1, rows, l, 3);
   }
