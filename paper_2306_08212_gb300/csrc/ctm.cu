@@ -1614,9 +1614,11 @@ std::vector<std::vector<double>> spectra_all(ctm_ctx* c) {
   }
   {
     ProfScope ps(c, 3, 0.0);
+    int* colver = (int*)dalloc(c, 4 * (long long)(ncols + 2));  // 8 x (ncols + 1) ints
     if (jacobi_batched(c->stream, X.t.p, nrows, ncols, 8, per, c->flags, kMaxSweeps,
-                       &c->launches, kValuesOnlyTol, true) != 0)
+                       &c->launches, kValuesOnlyTol, true, colver) != 0)
       fail(CTM_ERR_CUDA, "Jacobi launch failed");
+    dfree(c, colver);
   }
   Tmp sig(c, {8, ncols});
   int* perm = (int*)dalloc(c, 4 * ncols + 1);

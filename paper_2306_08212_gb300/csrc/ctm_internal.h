@@ -97,9 +97,12 @@ int jacobi_onesided(cudaStream_t s, double* X, int nrows, int ncols, double* V,
 // values alone converge quadratically in the cosines, so 1e-10 already gives
 // them to FP64 accuracy.
 // serialize: issue on the process-wide cooperative stream (see coop_stream).
+// colver (values-only mode): nprob * (ncols + 1) ints of scratch for per-column
+// step counters, which replace the grid barrier of every round-robin step; nullptr
+// keeps the barrier per step (no scratch needed).
 int jacobi_batched(cudaStream_t s, double* X, int nrows, int ncols, int nprob, long long pstride,
                    DevFlags* flags, int max_sweeps, long long* launches, double tol_override,
-                   bool serialize);
+                   bool serialize, int* colver = nullptr);
 
 // The stream on which every cooperative launch of this library runs (one per
 // device, created on first use).

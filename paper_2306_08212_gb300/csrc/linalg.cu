@@ -288,6 +288,135 @@ jacobi_warp_kernel(double* __restrict__ Xall, int nrows, int ncols, int npad, De
   }
 }
 
+// Values-only Jacobi without a grid barrier per round-robin step: column c of
+// problem p carries a step counter ver[p][c] (steps of all sweeps so far that
+// touched it).  The pair (i, j) of global step g waits, lane by lane with an
+// acquire load, until both counters read g (the previous step of each column is
+// done), rotates, then releases both counters to g + 1.  Warp w takes the pairs
+// w, w + nwarps, ... of every step, steps in order; all warps are resident (a
+// cooperative launch), so the earliest unfinished pair always has its inputs and
+// the waits end.  One grid barrier per sweep collects the largest off-diagonal
+// cosine for the stopping rule; every wait gives up after kBarrierCycleLimit
+// clocks, records the error and the kernel returns.
+__device__ __forceinline__ int ld_acquire_s32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_s32(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(kJacobiThreads)
+jacobi_flow_kernel(double* __restrict__ Xall, int nrows, int ncols, int npad, DevFlags* fl,
+                   int max_sweeps, double tol, int nprob, long long pstride, double tiny_rel,
+                   int* __restrict__ ver) {
+  const unsigned nblocks = gridDim.x;
+  const int npairs = npad / 2;
+  const int lane = threadIdx.x % 32;
+  const int gwarp = blockIdx.x * (kJacobiThreads / 32) + threadIdx.x / 32;
+  const int nwarps = gridDim.x * (kJacobiThreads / 32);
+  {
+    double part = 0.0, z1 = 0.0, z2 = 0.0;
+    const long long per = (long long)nrows * ncols;
+    for (int p = 0; p < nprob; ++p)
+      for (long long e = blockIdx.x * (long long)kJacobiThreads + threadIdx.x; e < per;
+           e += (long long)gridDim.x * kJacobiThreads)
+        part = fma(Xall[p * pstride + e], Xall[p * pstride + e], part);
+    block_sum3<kJacobiThreads>(part, z1, z2);
+    if (threadIdx.x == 0 && part > 0.0) atomicAdd(&fl->fro2, part);
+    if (!grid_barrier(fl, nblocks)) return;
+  }
+  const double tiny = tiny_rel * (*(volatile double*)&fl->fro2);
+  bool failed = false;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double local_max = 0.0;
+    for (int step = 0; step < npad - 1 && !failed; ++step) {
+      const int g = sweep * (npad - 1) + step;  // global step number
+      for (int kk = gwarp; kk < npairs * nprob; kk += nwarps) {
+        const int k = kk % npairs, p = kk / npairs;
+        double* X = Xall + (long long)p * pstride;
+        int* v = ver + (long long)p * npad;
+        const int i = rr_col(k, step, npad);
+        const int j = rr_col(npad - 1 - k, step, npad);
+        // wait for both columns to have finished the previous step
+        const long long t0 = clock64();
+        while (ld_acquire_s32(v + i) < g || ld_acquire_s32(v + j) < g) {
+          if (clock64() - t0 > kBarrierCycleLimit || *(volatile int*)&fl->error) {
+            atomicExch(&fl->error, 1);
+            failed = true;
+            break;
+          }
+        }
+        if (failed) break;
+        if (i < ncols && j < ncols) {
+          double* xi = X + (long long)i * nrows;
+          double* xj = X + (long long)j * nrows;
+          double a = 0.0, b = 0.0, gg = 0.0;
+          for (int r = lane; r < nrows; r += 32) {
+            const double u = xi[r], w = xj[r];
+            a = fma(u, u, a);
+            b = fma(w, w, b);
+            gg = fma(u, w, gg);
+          }
+          for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            gg += __shfl_xor_sync(0xffffffffu, gg, o);
+          }
+          if (a > 0.0 && b > 0.0) {
+            const double cosang = fabs(gg) / (sqrt(a) * sqrt(b));
+            if (a > tiny && b > tiny) local_max = fmax(local_max, cosang);
+            if (cosang > tol) {
+              const double zeta = (b - a) / (2.0 * gg);
+              const double t = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
+              const double c = 1.0 / sqrt(1.0 + t * t);
+              const double sn = c * t;
+              for (int r = lane; r < nrows; r += 32) {
+                const double u = xi[r], w = xj[r];
+                xi[r] = c * u - sn * w;
+                xj[r] = sn * u + c * w;
+              }
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence();
+          st_release_s32(v + i, g + 1);
+          st_release_s32(v + j, g + 1);
+        }
+        __syncwarp();
+      }
+    }
+    __shared__ double s_max[kJacobiThreads / 32];
+    for (int o = 16; o > 0; o >>= 1) local_max = fmax(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
+    if (lane == 0) s_max[threadIdx.x / 32] = local_max;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m = 0.0;
+      for (int w = 0; w < kJacobiThreads / 32; ++w) m = fmax(m, s_max[w]);
+      if (m > 0.0)
+        atomicMax(&fl->off_max[sweep & 1], (unsigned long long)__double_as_longlong(m));
+    }
+    if (!grid_barrier(fl, nblocks)) return;
+    const double m = __longlong_as_double(
+        (long long)(*(volatile unsigned long long*)&fl->off_max[sweep & 1]));
+    if (!(m > tol)) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) fl->sweeps = sweep + 1;
+      return;
+    }
+    // every block has read this sweep's maximum: clear the slot of the next sweep
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(&fl->off_max[(sweep + 1) & 1], 0ull);
+    if (!grid_barrier(fl, nblocks)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    fl->sweeps = max_sweeps;
+    atomicExch(&fl->noconv, 1);
+  }
+}
+
 __global__ void identity_kernel(double* x, int n) {
   const long long nn = (long long)n * n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nn;
@@ -305,7 +434,7 @@ cudaError_t fill_identity(cudaStream_t s, double* x, int n) {
 
 int jacobi_batched(cudaStream_t s, double* X, int nrows, int ncols, int nprob, long long pstride,
                    DevFlags* flags, int max_sweeps, long long* launches, double tol_override,
-                   bool serialize);
+                   bool serialize, int* colver);
 
 // Cooperative launches rely on all their blocks being resident at once; two of
 // them running together (different contexts or streams) could each hold SMs
@@ -426,7 +555,7 @@ int jacobi_onesided(cudaStream_t s, double* X, int nrows, int ncols, double* V, 
 // step serves all of them.
 int jacobi_batched(cudaStream_t s, double* X, int nrows, int ncols, int nprob, long long pstride,
                    DevFlags* flags, int max_sweeps, long long* launches, double tol_override,
-                   bool serialize) {
+                   bool serialize, int* colver) {
   if (ncols < 2 || nprob < 1) return 0;
   const int npad = ncols + (ncols & 1);
   int dev = 0, nsm = 0, per_sm = 0;
@@ -444,6 +573,17 @@ int jacobi_batched(cudaStream_t s, double* X, int nrows, int ncols, int nprob, l
                          : 2.220446049250313e-16 * std::sqrt((double)(nrows > 1 ? nrows : 1));
   double* V = nullptr;
   double tiny_rel = warp_mode ? 1e-24 : 1e-32;
+  if (warp_mode && colver) {  // step counters instead of a grid barrier per step
+    if (cudaMemsetAsync(colver, 0, sizeof(int) * (size_t)nprob * npad, s) != cudaSuccess)
+      return -3;
+    void* fargs[] = {&X, &nrows, &ncols, (void*)&npad, &flags, &max_sweeps, (void*)&tol,
+                     &nprob, &pstride, &tiny_rel, &colver};
+    if (launch_coop_ordered((void*)jacobi_flow_kernel, dim3(grid), dim3(kJacobiThreads), fargs, s,
+                            serialize) != cudaSuccess)
+      return -3;
+    ++*launches;
+    return 0;
+  }
   if (warp_mode) {
     void* wargs[] = {&X, &nrows, &ncols, (void*)&npad, &flags, &max_sweeps, (void*)&tol,
                      &nprob, &pstride, &tiny_rel, &V};

@@ -364,6 +364,45 @@ pack_kernel(void* __restrict__ out, const double* __restrict__ in, LegMap Rm, Le
   }
 }
 
+// Transposing variant for operands whose rows, not their K positions, are
+// contiguous in memory (the innermost row leg has unit stride): a block reads a
+// tile of 64 rows x 32 K-positions along the rows (coalesced), stages it in
+// shared memory and writes it along K.
+constexpr int kPackTR = 64, kPackTK = 32;
+
+template <bool TF32>
+__global__ void __launch_bounds__(256)
+pack_t_kernel(void* __restrict__ out, const double* __restrict__ in, LegMap Rm, LegMap Rk,
+              long long R, long long K, long long Kp) {
+  __shared__ long long offr[kPackTR];
+  __shared__ long long offk[kPackTK];
+  __shared__ double tile[kPackTK][kPackTR + 1];
+  const long long r0 = (long long)blockIdx.y * kPackTR;
+  const long long k0 = (long long)blockIdx.x * kPackTK;
+  for (int i = threadIdx.x; i < kPackTR; i += blockDim.x)
+    offr[i] = (r0 + i < R) ? tc_map_offset(Rm, r0 + i) : 0;
+  for (int i = threadIdx.x; i < kPackTK; i += blockDim.x)
+    offk[i] = (k0 + i < K) ? tc_map_offset(Rk, k0 + i) : 0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < kPackTR * kPackTK; e += blockDim.x) {
+    const int rr = e % kPackTR, kk = e / kPackTR;  // rows fastest: coalesced reads
+    const long long r = r0 + rr, k = k0 + kk;
+    tile[kk][rr] = (r < R && k < K) ? in[offr[rr] + offk[kk]] : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kPackTR * kPackTK; e += blockDim.x) {
+    const int kk = e % kPackTK, rr = e / kPackTK;  // K fastest: coalesced writes
+    const long long r = r0 + rr, k = k0 + kk;
+    if (r >= R || k >= Kp) continue;
+    const double v = tile[kk][rr];
+    const long long o = r * Kp + k;
+    if constexpr (TF32)
+      static_cast<float*>(out)[o] = round_tf32((float)v);
+    else
+      static_cast<__nv_bfloat16*>(out)[o] = __double2bfloat16(v);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -463,6 +502,14 @@ cudaError_t launch(cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb,
 template <bool TF32>
 cudaError_t pack(cudaStream_t s, void* out, const double* in, const LegMap& Rm, const LegMap& Rk,
                  long long R, long long K, long long Kp) {
+  const bool rows_contiguous = Rm.n > 0 && Rm.stride[Rm.n - 1] == 1 &&
+                               !(Rk.n > 0 && Rk.stride[Rk.n - 1] == 1);
+  if (rows_contiguous) {
+    const long long gy = (R + kPackTR - 1) / kPackTR, gx = (Kp + kPackTK - 1) / kPackTK;
+    if (gy > 65535 || gx > (1ll << 31) - 1) return cudaErrorInvalidConfiguration;
+    pack_t_kernel<TF32><<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(out, in, Rm, Rk, R, K, Kp);
+    return cudaGetLastError();
+  }
   const long long gy = (R + kPackRows - 1) / kPackRows, gx = (Kp + kPackK - 1) / kPackK;
   if (gy > 65535 || gx > (1ll << 31) - 1) return cudaErrorInvalidConfiguration;
   pack_kernel<TF32><<<dim3((unsigned)gx, (unsigned)gy), 256, 0, s>>>(out, in, Rm, Rk, R, K, Kp);
