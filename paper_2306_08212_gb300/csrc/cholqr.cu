@@ -39,7 +39,7 @@ namespace {
 
 constexpr int kCqThreads = 256;
 constexpr int kTb = 32;           // tile / panel width
-constexpr int kRowBlock = 16;     // rows per substitution block
+constexpr int kRowBlock = 16;     // rows per substitution block (two per thread column)
 constexpr double kNearIdentity = 1e-8;
 constexpr long long kCqBarrierLimit = 4000000000ll;  // clocks (~2 s)
 constexpr int kCqMaxN = kCholqrMaxN;
@@ -226,62 +226,76 @@ __device__ void reduce_scale(const CqArgs& a, double shift, int pass) {
   }
 }
 
-// Diagonal block p: Cholesky in place (lower) and its inverse into Linv[p], on
-// warp 0 of the calling block.  Pivot rules: shifted pass -> floor at `floor`
+// Diagonal block p: Cholesky in place (lower) and its inverse into Linv[p], by
+// every thread of the calling block: thread 0 takes each pivot, the column scaling
+// and the rank-1 update of the trailing triangle are spread over the block; the
+// inverse goes row by row, x_i = (e_i - sum_k L_ik x_k) / L_ii, each column's sum
+// split over eight partial sums.  Pivot rules: shifted pass -> floor at `floor`
 // (counted); unshifted passes -> a pivot <= tau marks a dependent column.
 __device__ void diag_factor(const CqArgs& a, const CqProb& P, int p, double floor, double tau,
                             bool use_mask) {
   __shared__ double L[kTb][kTb + 1];
   __shared__ double X[kTb][kTb + 1];
   __shared__ double rinv[kTb];
-  const int lane = threadIdx.x;
+  __shared__ double part[kCqThreads / kTb][kTb];
+  __shared__ int s_dep;
+  const int t = threadIdx.x;
   const int j0 = p * kTb, jb = min(kTb, a.n - j0);
-  if (threadIdx.x < 32) {
-    for (int j = 0; j < kTb; ++j)
-      L[lane][j] = (lane < jb && j < jb && j <= lane) ? P.G[(long long)(j0 + lane) * a.n + j0 + j]
-                                                      : 0.0;
-    __syncwarp();
-    for (int k = 0; k < jb; ++k) {
+  __syncthreads();
+  for (int e = t; e < kTb * kTb; e += kCqThreads) {
+    const int i = e / kTb, j = e % kTb;
+    L[i][j] = (i < jb && j < jb && j <= i) ? P.G[(long long)(j0 + i) * a.n + j0 + j] : 0.0;
+  }
+  __syncthreads();
+  for (int k = 0; k < jb; ++k) {
+    if (t == 0) {
       double dkk = L[k][k];
-      bool dep = false, floored = false;
-      if (use_mask && !(dkk > tau)) {
-        dep = true;
+      s_dep = 0;
+      if (use_mask && !(dkk > tau)) {  // column k lies in the span of the earlier ones
+        s_dep = 1;
+        P.defmask[j0 + k] = 1;
         dkk = 1.0;
       } else if (!(dkk > floor)) {
         dkk = floor;
-        floored = true;
+        atomicAdd(a.floored, 1);
       }
       const double piv = sqrt(dkk);
-      __syncwarp();
-      if (lane == k) {
-        L[k][k] = piv;
-        rinv[k] = 1.0 / piv;
-        if (dep) P.defmask[j0 + k] = 1;
-        if (floored) atomicAdd(a.floored, 1);
-      }
-      if (lane > k && lane < jb) L[lane][k] = dep ? 0.0 : L[lane][k] / piv;
-      __syncwarp();
-      if (lane > k && lane < jb) {
-        const double lik = L[lane][k];
-        for (int j = k + 1; j <= lane; ++j) L[lane][j] = fma(-lik, L[j][k], L[lane][j]);
-      }
-      __syncwarp();
+      L[k][k] = piv;
+      rinv[k] = 1.0 / piv;
     }
-    // inverse, column `lane`: x_i = (delta_{i,lane} - sum_{lane <= k < i} L_ik x_k) / L_ii
-    for (int i = 0; i < kTb; ++i) {
+    __syncthreads();
+    const int m = jb - k - 1;  // rows below the pivot
+    if (t < m) L[k + 1 + t][k] = s_dep ? 0.0 : L[k + 1 + t][k] * rinv[k];
+    __syncthreads();
+    for (int e = t; e < m * m; e += kCqThreads) {  // trailing triangle, k < j <= i < jb
+      const int i = k + 1 + e / m, j = k + 1 + e % m;
+      if (j <= i) L[i][j] = fma(-L[i][k], L[j][k], L[i][j]);
+    }
+    __syncthreads();
+  }
+  // inverse: thread t handles column c = t % 32 and the k's congruent to q = t / 32 mod 8
+  constexpr int NQ = kCqThreads / kTb;
+  const int c = t % kTb, q = t / kTb;
+  for (int i = 0; i < kTb; ++i) {
+    double acc = 0.0;
+    for (int k = c + q; k < i; k += NQ) acc = fma(-L[i][k], X[k][c], acc);
+    part[q][c] = acc;
+    __syncthreads();
+    if (q == 0) {
       double v = 0.0;
-      if (lane < jb && i < jb && i >= lane) {
-        double acc = (i == lane) ? 1.0 : 0.0;
-        for (int k = lane; k < i; ++k) acc = fma(-L[i][k], X[k][lane], acc);
-        v = acc * rinv[i];
+      if (i < jb && c <= i) {
+        double s = (i == c) ? 1.0 : 0.0;
+        for (int r = 0; r < NQ; ++r) s += part[r][c];
+        v = s * rinv[i];
       }
-      X[i][lane] = v;
-      __syncwarp();
+      X[i][c] = v;
     }
-    for (int i = 0; i < kTb; ++i) {
-      if (i < jb && lane < jb) P.G[(long long)(j0 + i) * a.n + j0 + lane] = lane <= i ? L[i][lane] : 0.0;
-      P.Linv[(long long)p * kTb * kTb + i * kTb + lane] = X[i][lane];
-    }
+    __syncthreads();
+  }
+  for (int e = t; e < kTb * kTb; e += kCqThreads) {
+    const int i = e / kTb, j = e % kTb;
+    if (i < jb && j < jb) P.G[(long long)(j0 + i) * a.n + j0 + j] = j <= i ? L[i][j] : 0.0;
+    P.Linv[(long long)p * kTb * kTb + e] = X[i][j];
   }
 }
 
