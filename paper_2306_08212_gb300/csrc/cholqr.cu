@@ -45,6 +45,22 @@ constexpr long long kCqBarrierLimit = 4000000000ll;  // clocks (~2 s)
 constexpr int kCqMaxN = kCholqrMaxN;
 
 constexpr int kCqMaxProb = kCholqrMaxProb;  // independent problems of one launch
+constexpr int kPitch = kTb + 1;             // shared-memory row pitch of 32-wide tiles
+
+// Every phase takes its shared memory from the one dynamic buffer (the phases
+// are separated by barriers), so that two CTAs fit on an SM when n <= 256.
+__device__ __forceinline__ double* cq_smem() {
+  extern __shared__ double cq_dyn[];
+  return cq_dyn;
+}
+
+// dynamic shared memory of a launch for n columns (the substitution phase is the
+// largest user: two 16-row blocks of the rows and two 32-wide tiles)
+__host__ __device__ constexpr size_t cq_smem_doubles(int n) {
+  return (size_t)2 * kRowBlock * n + kTb * kPitch + kRowBlock * kPitch > (size_t)2 * kTb * kPitch + kTb + kCqThreads
+             ? (size_t)2 * kRowBlock * n + kTb * kPitch + kRowBlock * kPitch
+             : (size_t)2 * kTb * kPitch + kTb + kCqThreads;
+}
 
 // Per-problem pointers (inputs, outputs and this problem's part of the work buffer).
 struct CqProb {
@@ -142,8 +158,8 @@ __device__ __forceinline__ int pair_index(int bi, int bj, int T) {  // bi <= bj
 // Phase G: partial Gram tiles of every problem.  Thread (ty, tx) of a 16 x 16
 // layout owns the 2 x 2 outputs (2ty + a, 2tx + b) of the 32 x 32 tile.
 __device__ void gram_partials(const CqArgs& a, int pass) {
-  __shared__ double As[kTb][kTb + 1];
-  __shared__ double Bs[kTb][kTb + 1];
+  double* As = cq_smem();                  // [kTb][kTb + 1]
+  double* Bs = As + kTb * kPitch;          // [kTb][kTb + 1]
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   const int per = a.npairs * a.nchunk;
   for (int item = blockIdx.x; item < a.nprob * per; item += gridDim.x) {
@@ -161,14 +177,14 @@ __device__ void gram_partials(const CqArgs& a, int pass) {
       for (int e = tid; e < kTb * kTb; e += kCqThreads) {
         const int rr = e / kTb, cc = e % kTb;
         const int r = rs + rr, ci = bi * kTb + cc, cj = bj * kTb + cc;
-        As[rr][cc] = (r < r1 && ci < a.n) ? X[(long long)r * a.n + ci] : 0.0;
-        Bs[rr][cc] = (r < r1 && cj < a.n) ? X[(long long)r * a.n + cj] : 0.0;
+        As[rr * kPitch + cc] = (r < r1 && ci < a.n) ? X[(long long)r * a.n + ci] : 0.0;
+        Bs[rr * kPitch + cc] = (r < r1 && cj < a.n) ? X[(long long)r * a.n + cj] : 0.0;
       }
       __syncthreads();
 #pragma unroll 8
       for (int rr = 0; rr < kTb; ++rr) {
-        const double a0 = As[rr][2 * ty], a1 = As[rr][2 * ty + 1];
-        const double b0 = Bs[rr][2 * tx], b1 = Bs[rr][2 * tx + 1];
+        const double a0 = As[rr * kPitch + 2 * ty], a1 = As[rr * kPitch + 2 * ty + 1];
+        const double b0 = Bs[rr * kPitch + 2 * tx], b1 = Bs[rr * kPitch + 2 * tx + 1];
         acc00 = fma(a0, b0, acc00);
         acc01 = fma(a0, b1, acc01);
         acc10 = fma(a1, b0, acc10);
@@ -234,22 +250,22 @@ __device__ void reduce_scale(const CqArgs& a, double shift, int pass) {
 // (counted); unshifted passes -> a pivot <= tau marks a dependent column.
 __device__ void diag_factor(const CqArgs& a, const CqProb& P, int p, double floor, double tau,
                             bool use_mask) {
-  __shared__ double L[kTb][kTb + 1];
-  __shared__ double X[kTb][kTb + 1];
-  __shared__ double rinv[kTb];
-  __shared__ double part[kCqThreads / kTb][kTb];
+  double* Lm = cq_smem();                  // [kTb][kTb + 1]
+  double* Xm = Lm + kTb * kPitch;          // [kTb][kTb + 1]
+  double* rinv = Xm + kTb * kPitch;        // [kTb]
+  double* part = rinv + kTb;               // [kCqThreads / kTb][kTb]
   __shared__ int s_dep;
   const int t = threadIdx.x;
   const int j0 = p * kTb, jb = min(kTb, a.n - j0);
   __syncthreads();
   for (int e = t; e < kTb * kTb; e += kCqThreads) {
     const int i = e / kTb, j = e % kTb;
-    L[i][j] = (i < jb && j < jb && j <= i) ? P.G[(long long)(j0 + i) * a.n + j0 + j] : 0.0;
+    Lm[(i) * kPitch + (j)] = (i < jb && j < jb && j <= i) ? P.G[(long long)(j0 + i) * a.n + j0 + j] : 0.0;
   }
   __syncthreads();
   for (int k = 0; k < jb; ++k) {
     if (t == 0) {
-      double dkk = L[k][k];
+      double dkk = Lm[(k) * kPitch + (k)];
       s_dep = 0;
       if (use_mask && !(dkk > tau)) {  // column k lies in the span of the earlier ones
         s_dep = 1;
@@ -260,16 +276,16 @@ __device__ void diag_factor(const CqArgs& a, const CqProb& P, int p, double floo
         atomicAdd(a.floored, 1);
       }
       const double piv = sqrt(dkk);
-      L[k][k] = piv;
+      Lm[(k) * kPitch + (k)] = piv;
       rinv[k] = 1.0 / piv;
     }
     __syncthreads();
     const int m = jb - k - 1;  // rows below the pivot
-    if (t < m) L[k + 1 + t][k] = s_dep ? 0.0 : L[k + 1 + t][k] * rinv[k];
+    if (t < m) Lm[(k + 1 + t) * kPitch + (k)] = s_dep ? 0.0 : Lm[(k + 1 + t) * kPitch + (k)] * rinv[k];
     __syncthreads();
     for (int e = t; e < m * m; e += kCqThreads) {  // trailing triangle, k < j <= i < jb
       const int i = k + 1 + e / m, j = k + 1 + e % m;
-      if (j <= i) L[i][j] = fma(-L[i][k], L[j][k], L[i][j]);
+      if (j <= i) Lm[(i) * kPitch + (j)] = fma(-Lm[(i) * kPitch + (k)], Lm[(j) * kPitch + (k)], Lm[(i) * kPitch + (j)]);
     }
     __syncthreads();
   }
@@ -278,32 +294,32 @@ __device__ void diag_factor(const CqArgs& a, const CqProb& P, int p, double floo
   const int c = t % kTb, q = t / kTb;
   for (int i = 0; i < kTb; ++i) {
     double acc = 0.0;
-    for (int k = c + q; k < i; k += NQ) acc = fma(-L[i][k], X[k][c], acc);
-    part[q][c] = acc;
+    for (int k = c + q; k < i; k += NQ) acc = fma(-Lm[(i) * kPitch + (k)], Xm[(k) * kPitch + (c)], acc);
+    part[(q) * kTb + (c)] = acc;
     __syncthreads();
     if (q == 0) {
       double v = 0.0;
       if (i < jb && c <= i) {
         double s = (i == c) ? 1.0 : 0.0;
-        for (int r = 0; r < NQ; ++r) s += part[r][c];
+        for (int r = 0; r < NQ; ++r) s += part[(r) * kTb + (c)];
         v = s * rinv[i];
       }
-      X[i][c] = v;
+      Xm[(i) * kPitch + (c)] = v;
     }
     __syncthreads();
   }
   for (int e = t; e < kTb * kTb; e += kCqThreads) {
     const int i = e / kTb, j = e % kTb;
-    if (i < jb && j < jb) P.G[(long long)(j0 + i) * a.n + j0 + j] = j <= i ? L[i][j] : 0.0;
-    P.Linv[(long long)p * kTb * kTb + e] = X[i][j];
+    if (i < jb && j < jb) P.G[(long long)(j0 + i) * a.n + j0 + j] = j <= i ? Lm[(i) * kPitch + (j)] : 0.0;
+    P.Linv[(long long)p * kTb * kTb + e] = Xm[(i) * kPitch + (j)];
   }
 }
 
 // Panel p: L_ip = G'_ip Linv_pp^T for block rows i > p of every problem that
 // takes the Cholesky (chol[q]); items are 8-row groups.
 __device__ void panel_solve(const CqArgs& a, int p, const bool* chol) {
-  __shared__ double Li[kTb][kTb + 1];
-  __shared__ double Gr[8][kTb + 1];
+  double* Li = cq_smem();                  // [kTb][kTb + 1]
+  double* Gr = Li + kTb * kPitch;          // [8][kTb + 1]
   const int tid = threadIdx.x;
   const int j0 = p * kTb, jb = min(kTb, a.n - j0);
   const int r_lo = j0 + jb;
@@ -315,17 +331,17 @@ __device__ void panel_solve(const CqArgs& a, int p, const bool* chol) {
     const int r0 = r_lo + (item % groups) * 8;
     __syncthreads();
     for (int e = tid; e < kTb * kTb; e += kCqThreads)
-      Li[e / kTb][e % kTb] = P.Linv[(long long)p * kTb * kTb + e];
+      Li[(e / kTb) * kPitch + e % kTb] = P.Linv[(long long)p * kTb * kTb + e];
     {
       const int rr = tid / kTb, cc = tid % kTb;
       const int r = r0 + rr;
-      Gr[rr][cc] = (r < a.n && cc < jb) ? P.G[(long long)r * a.n + j0 + cc] : 0.0;
+      Gr[rr * kPitch + cc] = (r < a.n && cc < jb) ? P.G[(long long)r * a.n + j0 + cc] : 0.0;
     }
     __syncthreads();
     const int rr = tid / kTb, cc = tid % kTb;
     double acc = 0.0;
 #pragma unroll 8
-    for (int k = 0; k < kTb; ++k) acc = fma(Gr[rr][k], Li[cc][k], acc);
+    for (int k = 0; k < kTb; ++k) acc = fma(Gr[rr * kPitch + k], Li[cc * kPitch + k], acc);
     const int r = r0 + rr;
     if (r < a.n && cc < jb) P.G[(long long)r * a.n + j0 + cc] = acc;
   }
@@ -334,8 +350,8 @@ __device__ void panel_solve(const CqArgs& a, int p, const bool* chol) {
 // Trailing update after panel p: G'_ij -= L_ip L_jp^T for p < bj <= bi (block
 // coordinates), lower blocks only; items are (problem, block pair, 8-row group).
 __device__ void trailing_update(const CqArgs& a, int p, const bool* chol) {
-  __shared__ double Lj[kTb][kTb + 1];
-  __shared__ double Lr[8][kTb + 1];
+  double* Lj = cq_smem();                  // [kTb][kTb + 1]
+  double* Lr = Lj + kTb * kPitch;          // [8][kTb + 1]
   const int tid = threadIdx.x;
   const int j0 = p * kTb, jb = min(kTb, a.n - j0);
   const int nb = a.T - p - 1;  // remaining block rows/cols
@@ -355,12 +371,12 @@ __device__ void trailing_update(const CqArgs& a, int p, const bool* chol) {
     for (int e = tid; e < kTb * kTb; e += kCqThreads) {
       const int rr = e / kTb, kk = e % kTb;
       const int r = bc * kTb + rr;
-      Lj[rr][kk] = (r < a.n && kk < jb) ? P.G[(long long)r * a.n + j0 + kk] : 0.0;
+      Lj[rr * kPitch + kk] = (r < a.n && kk < jb) ? P.G[(long long)r * a.n + j0 + kk] : 0.0;
     }
     {
       const int rr = tid / kTb, kk = tid % kTb;
       const int r = r0 + rr;
-      Lr[rr][kk] = (r < a.n && kk < jb) ? P.G[(long long)r * a.n + j0 + kk] : 0.0;
+      Lr[rr * kPitch + kk] = (r < a.n && kk < jb) ? P.G[(long long)r * a.n + j0 + kk] : 0.0;
     }
     __syncthreads();
     const int rr = tid / kTb, cc = tid % kTb;
@@ -368,7 +384,7 @@ __device__ void trailing_update(const CqArgs& a, int p, const bool* chol) {
     if (r < a.n && col < a.n && col <= r) {
       double acc = 0.0;
 #pragma unroll 8
-      for (int k = 0; k < kTb; ++k) acc = fma(Lr[rr][k], Lj[cc][k], acc);
+      for (int k = 0; k < kTb; ++k) acc = fma(Lr[rr * kPitch + k], Lj[cc * kPitch + k], acc);
       P.G[(long long)r * a.n + col] -= acc;
     }
   }
@@ -378,11 +394,10 @@ __device__ void trailing_update(const CqArgs& a, int p, const bool* chol) {
 // 16-row blocks this CTA owns; then, when asked, flagged columns become Gaussian.
 __device__ void substitute(const CqArgs& a, int pass, const bool* near_ids, const bool* refills,
                            unsigned long long seed) {
-  extern __shared__ double dyn[];
-  double* Xs = dyn;                      // [kRowBlock][n] scaled input rows
-  double* Qs = dyn + kRowBlock * a.n;    // [kRowBlock][n] output rows
-  __shared__ double Lt[kTb][kTb + 1];    // a 32 x 32 tile of L (or U^T)
-  __shared__ double Tt[kRowBlock][kTb + 1];
+  double* Xs = cq_smem();                  // [kRowBlock][n] scaled input rows
+  double* Qs = Xs + kRowBlock * a.n;       // [kRowBlock][n] output rows
+  double* Lt = Qs + kRowBlock * a.n;       // [kTb][kTb + 1] a tile of L (or U^T)
+  double* Tt = Lt + kTb * kPitch;          // [kRowBlock][kTb + 1]
   const int tid = threadIdx.x;
   const int nblk = (a.rows + kRowBlock - 1) / kRowBlock;
   for (int item = blockIdx.x; item < a.nprob * nblk; item += gridDim.x) {
@@ -407,13 +422,13 @@ __device__ void substitute(const CqArgs& a, int pass, const bool* near_ids, cons
       for (int k0 = 0; k0 < j0; k0 += kTb) {
         __syncthreads();
         for (int e = tid; e < kTb * kTb; e += kCqThreads) {
-          const int i = e / kTb, k = e % kTb;  // Lt[i][k] = L[j0 + i][k0 + k]
-          Lt[i][k] = (i < jb) ? P.G[(long long)(j0 + i) * a.n + k0 + k] : 0.0;
+          const int i = e / kTb, k = e % kTb;  // Lt[(i) * kPitch + (k)] = L[j0 + i][k0 + k]
+          Lt[(i) * kPitch + (k)] = (i < jb) ? P.G[(long long)(j0 + i) * a.n + k0 + k] : 0.0;
         }
         __syncthreads();
 #pragma unroll 8
         for (int k = 0; k < kTb; ++k) {
-          const double l = Lt[cc][k];
+          const double l = Lt[(cc) * kPitch + (k)];
           acc0 = fma(src[rr0 * a.n + k0 + k], l, acc0);
           acc1 = fma(src[(rr0 + 8) * a.n + k0 + k], l, acc1);
         }
@@ -423,11 +438,11 @@ __device__ void substitute(const CqArgs& a, int pass, const bool* near_ids, cons
         __syncthreads();
         for (int e = tid; e < kTb * kTb; e += kCqThreads) {
           const int i = e / kTb, k = e % kTb;
-          Lt[i][k] = (i < jb && k < i) ? P.G[(long long)(j0 + i) * a.n + j0 + k] : 0.0;
+          Lt[(i) * kPitch + (k)] = (i < jb && k < i) ? P.G[(long long)(j0 + i) * a.n + j0 + k] : 0.0;
         }
         __syncthreads();
         for (int k = 0; k < kTb; ++k) {
-          const double l = Lt[cc][k];
+          const double l = Lt[(cc) * kPitch + (k)];
           acc0 = fma(Xs[rr0 * a.n + j0 + k], l, acc0);
           acc1 = fma(Xs[(rr0 + 8) * a.n + j0 + k], l, acc1);
         }
@@ -437,18 +452,18 @@ __device__ void substitute(const CqArgs& a, int pass, const bool* near_ids, cons
         }
       } else {
         // T = xs_panel - Q_{<p} L_{p,<p}^T, then Q_panel = T Linv_pp^T
-        Tt[rr0][cc] = cc < jb ? Xs[rr0 * a.n + j0 + cc] - acc0 : 0.0;
-        Tt[rr0 + 8][cc] = cc < jb ? Xs[(rr0 + 8) * a.n + j0 + cc] - acc1 : 0.0;
+        Tt[(rr0) * kPitch + (cc)] = cc < jb ? Xs[rr0 * a.n + j0 + cc] - acc0 : 0.0;
+        Tt[(rr0 + 8) * kPitch + (cc)] = cc < jb ? Xs[(rr0 + 8) * a.n + j0 + cc] - acc1 : 0.0;
         __syncthreads();
         for (int e = tid; e < kTb * kTb; e += kCqThreads)
-          Lt[e / kTb][e % kTb] = P.Linv[(long long)p * kTb * kTb + e];
+          Lt[(e / kTb) * kPitch + (e % kTb)] = P.Linv[(long long)p * kTb * kTb + e];
         __syncthreads();
         double q0 = 0.0, q1 = 0.0;
 #pragma unroll 8
         for (int k = 0; k < kTb; ++k) {
-          const double l = Lt[cc][k];
-          q0 = fma(Tt[rr0][k], l, q0);
-          q1 = fma(Tt[rr0 + 8][k], l, q1);
+          const double l = Lt[(cc) * kPitch + (k)];
+          q0 = fma(Tt[(rr0) * kPitch + (k)], l, q0);
+          q1 = fma(Tt[(rr0 + 8) * kPitch + (k)], l, q1);
         }
         if (cc < jb) {
           Qs[rr0 * a.n + j0 + cc] = q0;
@@ -604,13 +619,13 @@ int cholqr_fused_batch(cudaStream_t s, int nprob, const double* const* Y, double
   a.err_out = err_word;
   a.floored = floored;
   a.seed = seed;
-  const size_t dyn = sizeof(double) * 2 * kRowBlock * (size_t)n;
+  const size_t dyn = sizeof(double) * cq_smem_doubles(n);
   static int attr_dev = -1;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return -3;
   if (attr_dev != dev) {
     if (cudaFuncSetAttribute(cholqr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(double) * 2 * kRowBlock * kCqMaxN)) != cudaSuccess)
+                             (int)(sizeof(double) * cq_smem_doubles(kCqMaxN))) != cudaSuccess)
       return -3;
     attr_dev = dev;
   }
@@ -619,10 +634,11 @@ int cholqr_fused_batch(cudaStream_t s, int nprob, const double* const* Y, double
           cudaSuccess ||
       per_sm < 1)
     return -3;
+  if (per_sm > 2) per_sm = 2;
   // this launch's barrier words start at zero
   if (cudaMemsetAsync(a.fl, 0, sizeof(DevFlags), s) != cudaSuccess) return -3;
   void* args[] = {&a};
-  if (launch_cooperative(reinterpret_cast<const void*>(cholqr_kernel), dim3(nsm),
+  if (launch_cooperative(reinterpret_cast<const void*>(cholqr_kernel), dim3(nsm * per_sm),
                          dim3(kCqThreads), args, dyn, s, t0, t1) != cudaSuccess)
     return -3;
   ++*launches;
