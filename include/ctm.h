@@ -192,7 +192,8 @@ long long ctm_kernel_launches(ctm_ctx* ctx);
  * events recorded on the context's stream around every launch of a class
  * (0 = FP64 contraction, 1 = TF32 tensor-core contraction, 2 = BF16 tensor-core
  * contraction, 3 = Jacobi SVD sweep kernel, 4 = fused FP64 CholeskyQR, whose
- * flop count is passes x (2 rows n^2 + n^3 / 3)).
+ * flop count, 2 rows n^2 + n^3 / 3 per pass it ran, is summed on the device:
+ * a problem stops after its first unshifted pass on a well-conditioned input).
  * ctm_profile_enable(ctx, mask) clears the counters and records the classes
  * whose bit (1 << class) is set in mask; 0 stops.  Changing the mask discards
  * the context's recorded CUDA graphs (they are recaptured with event nodes for

@@ -10,13 +10,19 @@
 //                                        pass of an ill-conditioned input
 //   G' = L L^T                          right-looking blocked Cholesky, 32-wide
 //                                        panels; the diagonal block and its inverse
-//                                        on one warp
+//                                        on one CTA per problem
 //   Q  = X D^-1 L^-T                    blocked forward substitution, each CTA
 //                                        owning 16-row blocks (no barrier inside)
 // When G' is within kNearIdentity of the identity (max |G' - I|, decided on the
 // device from the reduced Gram), L^-T = I - U + O(e^2) with U the strict upper
 // triangle of G' - I: the error e^2 <= 1e-16 is below FP64 rounding, so that
-// pass skips the Cholesky and computes Q = X D^-1 (I - U) directly.
+// pass skips the Cholesky and computes Q = X D^-1 (I - U) directly; below
+// kOrthonormal the input is orthonormal already and the pass only rescales it.
+//
+// Passes stop early per problem: an unshifted pass whose scaled Gram has
+// ||G' - I||_F <= kLastPassFro has kappa(G') <= (1 + f) / (1 - f) <= 3, so its
+// output is orthonormal to a small multiple of n u (the CholeskyQR bound is
+// proportional to kappa^2) and a further pass would not change it.
 //
 // Rank deficiency (unshifted passes): a pivot of the scaled Gram below tau marks
 // a column in the span of the earlier ones; its L column becomes e_k and, after a
@@ -30,6 +36,8 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdlib>
+#include <vector>
 
 #include "ctm_internal.h"
 
@@ -41,6 +49,8 @@ constexpr int kCqThreads = 256;
 constexpr int kTb = 32;           // tile / panel width
 constexpr int kRowBlock = 16;     // rows per substitution block (two per thread column)
 constexpr double kNearIdentity = 1e-8;
+constexpr double kOrthonormal = 1e-14;  // max |G' - I| of an input taken as orthonormal
+constexpr double kLastPassFro = 0.5;    // ||G' - I||_F that makes a pass the last one
 constexpr long long kCqBarrierLimit = 4000000000ll;  // clocks (~2 s)
 constexpr int kCqMaxN = kCholqrMaxN;
 
@@ -54,12 +64,13 @@ __device__ __forceinline__ double* cq_smem() {
   return cq_dyn;
 }
 
-// dynamic shared memory of a launch for n columns (the substitution phase is the
-// largest user: two 16-row blocks of the rows and two 32-wide tiles)
+// dynamic shared memory of a launch for n columns: the larger of the substitution
+// phase (two 16-row blocks of the rows and two tiles) and the diagonal factor
+// (three 32 x 32 tiles)
 __host__ __device__ constexpr size_t cq_smem_doubles(int n) {
-  return (size_t)2 * kRowBlock * n + kTb * kPitch + kRowBlock * kPitch > (size_t)2 * kTb * kPitch + kTb + kCqThreads
+  return (size_t)2 * kRowBlock * n + kTb * kPitch + kRowBlock * kPitch > (size_t)3 * kTb * kPitch + 2 * kTb
              ? (size_t)2 * kRowBlock * n + kTb * kPitch + kRowBlock * kPitch
-             : (size_t)2 * kTb * kPitch + kTb + kCqThreads;
+             : (size_t)3 * kTb * kPitch + 2 * kTb;
 }
 
 // Per-problem pointers (inputs, outputs and this problem's part of the work buffer).
@@ -70,7 +81,9 @@ struct CqProb {
   double* G;        // n x n, lower triangle used
   double* Linv;     // [T][32 * 32]
   double* dscale;   // n
+  double* dinv;     // n, 1 / dscale
   double* emax;     // [passes] max |G' - I| (bits of a non-negative double)
+  double* fro2;     // [passes] ||G' - I||_F^2
   int* defmask;     // n
 };
 
@@ -82,6 +95,8 @@ struct CqArgs {
   DevFlags* fl;     // this launch's own barrier words (inside the work buffer)
   int* err_out;     // sticky error word of the caller (set on a barrier timeout)
   int* floored;
+  double* flops_out;  // executed FP64 flops are added here (may be null)
+  unsigned long long* stamps;  // diagnostics (may be null): [0] count, then (tag, ns) pairs
   unsigned long long seed;
 };
 
@@ -157,13 +172,13 @@ __device__ __forceinline__ int pair_index(int bi, int bj, int T) {  // bi <= bj
 
 // Phase G: partial Gram tiles of every problem.  Thread (ty, tx) of a 16 x 16
 // layout owns the 2 x 2 outputs (2ty + a, 2tx + b) of the 32 x 32 tile.
-__device__ void gram_partials(const CqArgs& a, int pass) {
+__device__ void gram_partials(const CqArgs& a, int pass, const int* act, int nact) {
   double* As = cq_smem();                  // [kTb][kTb + 1]
   double* Bs = As + kTb * kPitch;          // [kTb][kTb + 1]
   const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   const int per = a.npairs * a.nchunk;
-  for (int item = blockIdx.x; item < a.nprob * per; item += gridDim.x) {
-    const CqProb& P = a.prob[item / per];
+  for (int item = blockIdx.x; item < nact * per; item += gridDim.x) {
+    const CqProb& P = a.prob[act[item / per]];
     const double* __restrict__ X = pass == 0 ? P.Y : P.Q;
     const int local = item % per;
     const int pair = local % a.npairs, chunk = local / a.npairs;
@@ -214,13 +229,13 @@ __device__ __forceinline__ double gram_entry(const CqArgs& a, const CqProb& P, i
   return s;
 }
 
-// Phase R: G' (lower triangle) = D^-1 G D^-1 + shift I, D, and max |G' - I|, for
-// every problem.
-__device__ void reduce_scale(const CqArgs& a, double shift, int pass) {
+// Phase R: G' (lower triangle) = D^-1 G D^-1 + shift I, D, max |G' - I| and
+// ||G' - I||_F^2, for every active problem.
+__device__ void reduce_scale(const CqArgs& a, double shift, int pass, const int* act, int nact) {
   const long long nn = (long long)a.n * a.n;
-  for (int p = 0; p < a.nprob; ++p) {
-    const CqProb& P = a.prob[p];
-    double local = 0.0;
+  for (int ia = 0; ia < nact; ++ia) {
+    const CqProb& P = a.prob[act[ia]];
+    double local = 0.0, sq = 0.0;
     for (long long e = blockIdx.x * (long long)kCqThreads + threadIdx.x; e < nn;
          e += (long long)gridDim.x * kCqThreads) {
       const int i = (int)(e / a.n), j = (int)(e % a.n);
@@ -231,87 +246,136 @@ __device__ void reduce_scale(const CqArgs& a, double shift, int pass) {
       if (i == j) {
         v += shift;
         P.dscale[i] = di;
+        P.dinv[i] = 1.0 / di;
       }
       P.G[(long long)i * a.n + j] = v;
-      local = fmax(local, fabs(v - (i == j ? 1.0 : 0.0)));
+      const double dev = v - (i == j ? 1.0 : 0.0);
+      local = fmax(local, fabs(dev));
+      sq = fma(i == j ? 1.0 : 2.0, dev * dev, sq);  // G' - I is symmetric
     }
-    for (int o = 16; o > 0; o >>= 1) local = fmax(local, __shfl_xor_sync(0xffffffffu, local, o));
+    for (int o = 16; o > 0; o >>= 1) {
+      local = fmax(local, __shfl_xor_sync(0xffffffffu, local, o));
+      sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    }
     if ((threadIdx.x & 31) == 0 && local > 0.0)
       atomicMax(reinterpret_cast<unsigned long long*>(P.emax + pass),
                 (unsigned long long)__double_as_longlong(local));
+    if ((threadIdx.x & 31) == 0 && sq > 0.0) atomicAdd(P.fro2 + pass, sq);
   }
 }
 
-// Diagonal block p: Cholesky in place (lower) and its inverse into Linv[p], by
-// every thread of the calling block: thread 0 takes each pivot, the column scaling
-// and the rank-1 update of the trailing triangle are spread over the block; the
-// inverse goes row by row, x_i = (e_i - sum_k L_ik x_k) / L_ii, each column's sum
-// split over eight partial sums.  Pivot rules: shifted pass -> floor at `floor`
-// (counted); unshifted passes -> a pivot <= tau marks a dependent column.
+// 1 / sqrt(d) for d in [1e-30, 1e30] (every pivot of a scaled Gram): the FP32
+// hardware estimate refined by two Newton-Raphson steps for the reciprocal
+// square root, y <- y + y (1 - d y^2) / 2, whose error squares at each step
+// (2^-22 -> 2^-44 -> below FP64 rounding).  On the pivot chain of the Cholesky
+// this replaces an FP64 square root and a division.
+__device__ __forceinline__ double cq_rsqrt(double d) {
+  double y = (double)rsqrtf((float)d);
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const double r = fma(-d * y, y, 1.0);
+    y = fma(0.5 * y, r, y);
+  }
+  return y;
+}
+
+// Diagonal block p: Cholesky (lower) and its inverse into Linv[p] by one CTA.
+// GB300 retires well under one FP64 warp-instruction per clock per SM
+// sub-partition, so what sets this phase's length is the chain of 32 pivots
+// and the FP64 instructions queued beside it.  Thread 0 (warp 0) only runs the
+// pivot chain, one step ahead: while the other warps apply step k, it updates
+// the next diagonal entry and takes its reciprocal square root.  Warps 1-3 and
+// 5-7 (the sub-partitions warp 0 does not use) apply step k: column k of the
+// factor, the rank-1 update of the trailing triangle of the working copy Lm,
+// and the same elimination on the rows of X, which starts as the identity and
+// ends as L^-1 (Gauss-Jordan on the unit matrix; row k's own scaling by
+// 1 / L_kk is applied once at the end).  One barrier per step.  Pivot rules:
+// shifted pass -> floor at `floor` (counted); unshifted passes -> a pivot
+// <= tau marks a dependent column (its L column is e_k).
+__device__ __forceinline__ void cq_pivot(const CqArgs& a, const CqProb& P, int col, double d,
+                                         double floor, double tau, bool use_mask, double* s_d,
+                                         double* s_y, int* s_dep, int k) {
+  int dep = 0;
+  if (use_mask && !(d > tau)) {  // column lies in the span of the earlier ones
+    dep = 1;
+    d = 1.0;
+    P.defmask[col] = 1;
+  } else if (!(d > floor)) {
+    d = floor;
+    atomicAdd(a.floored, 1);
+  }
+  s_d[k] = d;
+  s_y[k] = cq_rsqrt(d);
+  s_dep[k] = dep;
+}
+
 __device__ void diag_factor(const CqArgs& a, const CqProb& P, int p, double floor, double tau,
                             bool use_mask) {
-  double* Lm = cq_smem();                  // [kTb][kTb + 1]
-  double* Xm = Lm + kTb * kPitch;          // [kTb][kTb + 1]
-  double* rinv = Xm + kTb * kPitch;        // [kTb]
-  double* part = rinv + kTb;               // [kCqThreads / kTb][kTb]
-  __shared__ int s_dep;
-  const int t = threadIdx.x;
+  double* Lm = cq_smem();                  // [kTb][kTb + 1] working copy
+  double* Lo = Lm + kTb * kPitch;          // [kTb][kTb + 1] the factor
+  double* Xm = Lo + kTb * kPitch;          // [kTb][kTb + 1] its inverse
+  double* s_d = Xm + kTb * kPitch;         // [kTb] pivots after the rules
+  double* s_y = s_d + kTb;                 // [kTb] 1 / sqrt(pivot)
+  __shared__ int s_dep[kTb];
+  const int t = threadIdx.x, warp = t / 32;
   const int j0 = p * kTb, jb = min(kTb, a.n - j0);
+  // workers: warps not on warp 0's sub-partition
+  const bool worker = (warp % 4) != 0;
+  const int wid = (warp / 4) * 96 + (warp % 4 - 1) * 32 + t % 32;  // 0 .. 191
+  constexpr int kWorkers = kCqThreads / 4 * 3;
   __syncthreads();
   for (int e = t; e < kTb * kTb; e += kCqThreads) {
     const int i = e / kTb, j = e % kTb;
-    Lm[(i) * kPitch + (j)] = (i < jb && j < jb && j <= i) ? P.G[(long long)(j0 + i) * a.n + j0 + j] : 0.0;
+    Lm[i * kPitch + j] = (i < jb && j < jb && j <= i) ? P.G[(long long)(j0 + i) * a.n + j0 + j] : 0.0;
+    Lo[i * kPitch + j] = 0.0;
+    Xm[i * kPitch + j] = (i == j && i < jb) ? 1.0 : 0.0;
   }
+  __syncthreads();
+  if (t == 0) cq_pivot(a, P, j0, Lm[0], floor, tau, use_mask, s_d, s_y, s_dep, 0);
   __syncthreads();
   for (int k = 0; k < jb; ++k) {
-    if (t == 0) {
-      double dkk = Lm[(k) * kPitch + (k)];
-      s_dep = 0;
-      if (use_mask && !(dkk > tau)) {  // column k lies in the span of the earlier ones
-        s_dep = 1;
-        P.defmask[j0 + k] = 1;
-        dkk = 1.0;
-      } else if (!(dkk > floor)) {
-        dkk = floor;
-        atomicAdd(a.floored, 1);
-      }
-      const double piv = sqrt(dkk);
-      Lm[(k) * kPitch + (k)] = piv;
-      rinv[k] = 1.0 / piv;
-    }
-    __syncthreads();
+    const double y = s_y[k];
+    const bool dep = s_dep[k] != 0;
     const int m = jb - k - 1;  // rows below the pivot
-    if (t < m) Lm[(k + 1 + t) * kPitch + (k)] = s_dep ? 0.0 : Lm[(k + 1 + t) * kPitch + (k)] * rinv[k];
-    __syncthreads();
-    for (int e = t; e < m * m; e += kCqThreads) {  // trailing triangle, k < j <= i < jb
-      const int i = k + 1 + e / m, j = k + 1 + e % m;
-      if (j <= i) Lm[(i) * kPitch + (j)] = fma(-Lm[(i) * kPitch + (k)], Lm[(j) * kPitch + (k)], Lm[(i) * kPitch + (j)]);
-    }
-    __syncthreads();
-  }
-  // inverse: thread t handles column c = t % 32 and the k's congruent to q = t / 32 mod 8
-  constexpr int NQ = kCqThreads / kTb;
-  const int c = t % kTb, q = t / kTb;
-  for (int i = 0; i < kTb; ++i) {
-    double acc = 0.0;
-    for (int k = c + q; k < i; k += NQ) acc = fma(-Lm[(i) * kPitch + (k)], Xm[(k) * kPitch + (c)], acc);
-    part[(q) * kTb + (c)] = acc;
-    __syncthreads();
-    if (q == 0) {
-      double v = 0.0;
-      if (i < jb && c <= i) {
-        double s = (i == c) ? 1.0 : 0.0;
-        for (int r = 0; r < NQ; ++r) s += part[(r) * kTb + (c)];
-        v = s * rinv[i];
+    if (t == 0) {
+      Lo[k * kPitch + k] = s_d[k] * y;
+      if (m > 0) {
+        double d1 = Lm[(k + 1) * kPitch + k + 1];
+        if (!dep) {
+          const double l = Lm[(k + 1) * kPitch + k] * y;
+          d1 = fma(-l, l, d1);
+        }
+        cq_pivot(a, P, j0 + k + 1, d1, floor, tau, use_mask, s_d, s_y, s_dep, k + 1);
       }
-      Xm[(i) * kPitch + (c)] = v;
+    } else if (worker) {
+      const double y2 = y * y;
+      const int ntri = m * (m + 1) / 2;  // (i, j), k < j <= i < jb; entry 0 is the next pivot
+      const int nx = m * (k + 1);        // (i, c), k < i < jb, c <= k
+      for (int e = wid; e < ntri + nx + m; e += kWorkers) {
+        if (e < ntri) {
+          if (e == 0 || dep) continue;
+          int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+          if (r * (r + 1) / 2 > e) --r;
+          if ((r + 1) * (r + 2) / 2 <= e) ++r;
+          const int i = k + 1 + r, j = k + 1 + (e - r * (r + 1) / 2);
+          Lm[i * kPitch + j] = fma(-Lm[i * kPitch + k] * y2, Lm[j * kPitch + k], Lm[i * kPitch + j]);
+        } else if (e < ntri + nx) {
+          if (dep) continue;
+          const int e2 = e - ntri;
+          const int i = k + 1 + e2 / (k + 1), c = e2 % (k + 1);
+          Xm[i * kPitch + c] = fma(-Lm[i * kPitch + k] * y2, Xm[k * kPitch + c], Xm[i * kPitch + c]);
+        } else {
+          const int i = k + 1 + (e - ntri - nx);
+          Lo[i * kPitch + k] = dep ? 0.0 : Lm[i * kPitch + k] * y;
+        }
+      }
     }
     __syncthreads();
   }
   for (int e = t; e < kTb * kTb; e += kCqThreads) {
     const int i = e / kTb, j = e % kTb;
-    if (i < jb && j < jb) P.G[(long long)(j0 + i) * a.n + j0 + j] = j <= i ? Lm[(i) * kPitch + (j)] : 0.0;
-    P.Linv[(long long)p * kTb * kTb + e] = Xm[(i) * kPitch + (j)];
+    if (i < jb && j < jb) P.G[(long long)(j0 + i) * a.n + j0 + j] = Lo[i * kPitch + j];
+    P.Linv[(long long)p * kTb * kTb + e] = (i < jb && j <= i) ? Xm[i * kPitch + j] * s_y[i] : 0.0;
   }
 }
 
@@ -393,24 +457,32 @@ __device__ void trailing_update(const CqArgs& a, int p, const bool* chol) {
 // Phase T: Q = X D^-1 L^-T (full) or Q = X D^-1 (I - U) (near identity) for the
 // 16-row blocks this CTA owns; then, when asked, flagged columns become Gaussian.
 __device__ void substitute(const CqArgs& a, int pass, const bool* near_ids, const bool* refills,
-                           unsigned long long seed) {
+                           const bool* scale_only, unsigned long long seed, const int* act,
+                           int nact) {
   double* Xs = cq_smem();                  // [kRowBlock][n] scaled input rows
   double* Qs = Xs + kRowBlock * a.n;       // [kRowBlock][n] output rows
   double* Lt = Qs + kRowBlock * a.n;       // [kTb][kTb + 1] a tile of L (or U^T)
   double* Tt = Lt + kTb * kPitch;          // [kRowBlock][kTb + 1]
   const int tid = threadIdx.x;
   const int nblk = (a.rows + kRowBlock - 1) / kRowBlock;
-  for (int item = blockIdx.x; item < a.nprob * nblk; item += gridDim.x) {
-    const int q = item / nblk;
+  for (int item = blockIdx.x; item < nact * nblk; item += gridDim.x) {
+    const int q = act[item / nblk];
     const CqProb& P = a.prob[q];
     const double* __restrict__ X = pass == 0 ? P.Y : P.Q;
     const bool near_id = near_ids[q], refill = refills[q];
     const int r0 = (item % nblk) * kRowBlock;
+    if (scale_only[q]) {  // orthonormal input: Q = X D^-1, element by element
+      for (int e = tid; e < kRowBlock * a.n; e += kCqThreads) {
+        const int r = r0 + e / a.n, cc = e % a.n;
+        if (r < a.rows) P.Q[(long long)r * a.n + cc] = X[(long long)r * a.n + cc] * P.dinv[cc];
+      }
+      continue;
+    }
     __syncthreads();
     for (int e = tid; e < kRowBlock * a.n; e += kCqThreads) {
       const int rr = e / a.n, cc = e % a.n;
       const int r = r0 + rr;
-      Xs[e] = r < a.rows ? X[(long long)r * a.n + cc] / P.dscale[cc] : 0.0;
+      Xs[e] = r < a.rows ? X[(long long)r * a.n + cc] * P.dinv[cc] : 0.0;
     }
     __syncthreads();
     for (int p = 0; p < a.T; ++p) {
@@ -486,6 +558,20 @@ __device__ void substitute(const CqArgs& a, int pass, const bool* near_ids, cons
 
 __device__ bool cholqr_passes(const CqArgs& a, double u);
 
+constexpr int kCqMaxStamps = 512;
+
+// Diagnostics: block 0 records the global timer after each grid barrier.
+__device__ __forceinline__ void cq_stamp(const CqArgs& a, int tag) {
+  if (!a.stamps || blockIdx.x != 0 || threadIdx.x != 0) return;
+  const unsigned long long k = a.stamps[0];
+  if (k >= kCqMaxStamps) return;
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  a.stamps[1 + 2 * k] = (unsigned long long)tag;
+  a.stamps[2 + 2 * k] = t;
+  a.stamps[0] = k + 1;
+}
+
 __global__ void __launch_bounds__(kCqThreads, 1) cholqr_kernel(CqArgs a) {
   const double u = 1.1102230246251565e-16;
   const bool ok = cholqr_passes(a, u);
@@ -493,32 +579,56 @@ __global__ void __launch_bounds__(kCqThreads, 1) cholqr_kernel(CqArgs a) {
 }
 
 __device__ bool cholqr_passes(const CqArgs& a, double u) {
-  __shared__ bool s_chol[kCqMaxProb], s_near[kCqMaxProb], s_refill[kCqMaxProb];
-  for (int pass = 0; pass < a.passes; ++pass) {
+  __shared__ bool s_chol[kCqMaxProb], s_near[kCqMaxProb], s_refill[kCqMaxProb],
+      s_scale[kCqMaxProb], s_last[kCqMaxProb];
+  __shared__ int s_act[kCqMaxProb], s_nact;
+  double flops = 0.0;  // block 0, thread 0: flops of the passes run
+  const double gram = (double)a.rows * a.n * a.n, chol = (double)a.n * a.n * a.n / 3.0;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < a.nprob; ++q) s_act[q] = q;
+    s_nact = a.nprob;
+  }
+  __syncthreads();
+  cq_stamp(a, 0);
+  for (int pass = 0; pass < a.passes && s_nact > 0; ++pass) {
     const bool shift_pass = pass == 0 && a.shifted;
-    gram_partials(a, pass);
+    gram_partials(a, pass, s_act, s_nact);
     if (!cq_barrier(a.fl)) return false;
+    cq_stamp(a, 1);
     // the masks of the previous pass have been read by every block by now
     for (int q = 0; q < a.nprob; ++q)
       for (int j = blockIdx.x * kCqThreads + threadIdx.x; j < a.n; j += gridDim.x * kCqThreads)
         a.prob[q].defmask[j] = 0;
     const double shift =
         shift_pass ? 11.0 * ((double)a.rows * a.n + (double)a.n * (a.n + 1)) * u * a.n : 0.0;
-    reduce_scale(a, shift, pass);
+    reduce_scale(a, shift, pass, s_act, s_nact);
     if (!cq_barrier(a.fl)) return false;
+    cq_stamp(a, 2);
     // every block must take the same branches (the barrier count depends on them):
     // thread 0 reads each reduced maximum with an acquire load and broadcasts it
     if (threadIdx.x == 0) {
       for (int q = 0; q < a.nprob; ++q) {
-        unsigned long long bits;
+        s_near[q] = s_chol[q] = s_refill[q] = s_scale[q] = s_last[q] = false;
+      }
+      for (int ia = 0; ia < s_nact; ++ia) {
+        const int q = s_act[ia];
+        unsigned long long bits, fbits;
         asm volatile("ld.acquire.gpu.global.u64 %0, [%1];"
                      : "=l"(bits)
                      : "l"(a.prob[q].emax + pass)
                      : "memory");
+        asm volatile("ld.acquire.gpu.global.u64 %0, [%1];"
+                     : "=l"(fbits)
+                     : "l"(a.prob[q].fro2 + pass)
+                     : "memory");
         const double e = __longlong_as_double((long long)bits);
+        const double f2 = __longlong_as_double((long long)fbits);
         s_near[q] = !shift_pass && e < kNearIdentity;
+        s_scale[q] = !shift_pass && e < kOrthonormal;
         s_chol[q] = !s_near[q];
-        s_refill[q] = !s_near[q] && pass > 0 && pass + 1 < a.passes;
+        s_last[q] = !shift_pass && (s_scale[q] || f2 <= kLastPassFro * kLastPassFro);
+        s_refill[q] = !s_near[q] && !s_last[q] && pass > 0 && pass + 1 < a.passes;
+        flops += s_scale[q] ? gram : 2.0 * gram + (s_chol[q] ? chol : 0.0);
       }
     }
     __syncthreads();
@@ -526,25 +636,40 @@ __device__ bool cholqr_passes(const CqArgs& a, double u) {
     for (int q = 0; q < a.nprob; ++q) any_chol = any_chol || s_chol[q];
     if (any_chol) {
       for (int p = 0; p < a.T; ++p) {
-        if (blockIdx.x < a.nprob && s_chol[blockIdx.x])
+        if (blockIdx.x < a.nprob && s_chol[blockIdx.x])  // inactive problems: s_chol false
           diag_factor(a, a.prob[blockIdx.x], p, 1e-28, 1e-12, !shift_pass && pass > 0);
         if (!cq_barrier(a.fl)) return false;
+        cq_stamp(a, 3);
         panel_solve(a, p, s_chol);
         if (!cq_barrier(a.fl)) return false;
+        cq_stamp(a, 4);
         if (p + 1 < a.T) {
           trailing_update(a, p, s_chol);
           if (!cq_barrier(a.fl)) return false;
+          cq_stamp(a, 5);
         }
       }
     }
-    substitute(a, pass, s_near, s_refill, a.seed + (unsigned long long)pass);
+    substitute(a, pass, s_near, s_refill, s_scale, a.seed + (unsigned long long)pass, s_act,
+               s_nact);
     if (!cq_barrier(a.fl)) return false;
+    cq_stamp(a, 6);
+    // problems whose pass was their last leave the active list (same in every block)
+    if (threadIdx.x == 0) {
+      int n = 0;
+      for (int ia = 0; ia < s_nact; ++ia)
+        if (!s_last[s_act[ia]]) s_act[n++] = s_act[ia];
+      s_nact = n;
+    }
+    __syncthreads();
   }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && a.flops_out) atomicAdd(a.flops_out, flops);
   return true;
 }
 
 // Work layout (doubles): Gram partials | G' (n x n) | diagonal-block inverses |
-// D | max |G' - I| per pass (8) | dependent-column mask (n ints) | barrier words.
+// D | D^-1 | max |G' - I| per pass (8) | ||G' - I||_F^2 per pass (8) |
+// dependent-column mask (n ints) | barrier words.
 void cholqr_layout(int rows, int n, int nsm, int& T, int& npairs, int& nchunk, int& chunk_rows) {
   T = (n + kTb - 1) / kTb;
   npairs = T * (T + 1) / 2;
@@ -571,7 +696,7 @@ size_t cholqr_prob_doubles(int rows, int n) {
   const int nsm = cholqr_sm_count();
   int T, npairs, nchunk, chunk_rows;
   cholqr_layout(rows, n, nsm > 0 ? nsm : 1, T, npairs, nchunk, chunk_rows);
-  return (size_t)nchunk * npairs * kTb * kTb + (size_t)n * n + (size_t)T * kTb * kTb + n + 8 +
+  return (size_t)nchunk * npairs * kTb * kTb + (size_t)n * n + (size_t)T * kTb * kTb + 2 * n + 16 +
          (size_t)(n + 1) / 2;
 }
 
@@ -581,8 +706,8 @@ size_t cholqr_work_doubles(int rows, int n, int nprob) {
 
 int cholqr_fused_batch(cudaStream_t s, int nprob, const double* const* Y, double* const* Q,
                        int rows, int n, int passes, bool shifted, double* work, int* err_word,
-                       int* floored, unsigned long long seed, long long* launches, cudaEvent_t t0,
-                       cudaEvent_t t1) {
+                       int* floored, double* flops_out, unsigned long long seed,
+                       long long* launches, cudaEvent_t t0, cudaEvent_t t1) {
   if (nprob < 1 || nprob > kCqMaxProb || n < 1 || n > kCqMaxN || rows < 1 || passes < 1 ||
       passes > 8)
     return -1;
@@ -609,15 +734,20 @@ int cholqr_fused_batch(cudaStream_t s, int nprob, const double* const* Y, double
     w += (size_t)a.T * kTb * kTb;
     P.dscale = w;
     w += n;
+    P.dinv = w;
+    w += n;
     P.emax = w;
-    w += 8;
+    P.fro2 = w + 8;
+    w += 16;
     P.defmask = reinterpret_cast<int*>(w);
-    if (cudaMemsetAsync(P.emax, 0, 8 * sizeof(double), s) != cudaSuccess) return -3;
+    if (cudaMemsetAsync(P.emax, 0, 16 * sizeof(double), s) != cudaSuccess) return -3;
   }
   a.fl = reinterpret_cast<DevFlags*>(work + (size_t)nprob * per);
   static_assert(sizeof(DevFlags) <= 8 * sizeof(double), "DevFlags must fit its slot");
   a.err_out = err_word;
   a.floored = floored;
+  a.flops_out = flops_out;
+  a.stamps = cq_stamps_buffer();
   a.seed = seed;
   const size_t dyn = sizeof(double) * cq_smem_doubles(n);
   static int attr_dev = -1;
@@ -645,11 +775,59 @@ int cholqr_fused_batch(cudaStream_t s, int nprob, const double* const* Y, double
   return 0;
 }
 
+// CTM_TRACE=3: a device buffer of phase timestamps for the next launches.
+namespace {
+unsigned long long* g_stamps = nullptr;
+}
+unsigned long long* cq_stamps_buffer() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = std::getenv("CTM_TRACE");
+    on = (e && *e == '3') ? 1 : 0;
+  }
+  if (!on) return nullptr;
+  if (!g_stamps && cudaMalloc(&g_stamps, sizeof(unsigned long long) * (1 + 2 * kCqMaxStamps)) != cudaSuccess)
+    g_stamps = nullptr;
+  if (g_stamps) cudaMemset(g_stamps, 0, sizeof(unsigned long long));
+  return g_stamps;
+}
+
+int cholqr_read_stamps(cudaStream_t s, double* ms_by_tag /* [8] */) {
+  if (!g_stamps) return -1;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return -3;
+  std::vector<unsigned long long> h(1 + 2 * kCqMaxStamps);
+  if (cudaMemcpy(h.data(), g_stamps, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return -3;
+  for (int t = 0; t < 8; ++t) ms_by_tag[t] = 0.0;
+  const unsigned long long k = h[0] < (unsigned long long)kCqMaxStamps ? h[0] : kCqMaxStamps;
+  for (unsigned long long i = 1; i < k; ++i) {
+    const int tag = (int)h[1 + 2 * i];
+    ms_by_tag[tag & 7] += 1e-6 * (double)(h[2 + 2 * i] - h[2 * i]);
+  }
+  return 0;
+}
+
+int cholqr_read_emax(cudaStream_t s, const double* work, int rows, int n, int nprob, double* out) {
+  const int nsm = cholqr_sm_count();
+  if (nsm < 1 || nprob < 1 || nprob > kCqMaxProb) return -1;
+  int T, npairs, nchunk, chunk_rows;
+  cholqr_layout(rows, n, nsm, T, npairs, nchunk, chunk_rows);
+  const size_t off =
+      (size_t)nchunk * npairs * kTb * kTb + (size_t)n * n + (size_t)T * kTb * kTb + 2 * (size_t)n;
+  const size_t per = cholqr_prob_doubles(rows, n);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return -3;
+  for (int q = 0; q < nprob; ++q)
+    if (cudaMemcpy(out + 16 * q, work + q * per + off, 16 * sizeof(double), cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
+      return -3;
+  return 0;
+}
+
 int cholqr_fused(cudaStream_t s, const double* Y, double* Q, int rows, int n, int passes,
-                 bool shifted, double* work, int* err_word, int* floored, unsigned long long seed,
-                 long long* launches, cudaEvent_t t0, cudaEvent_t t1) {
-  return cholqr_fused_batch(s, 1, &Y, &Q, rows, n, passes, shifted, work, err_word, floored, seed,
-                            launches, t0, t1);
+                 bool shifted, double* work, int* err_word, int* floored, double* flops_out,
+                 unsigned long long seed, long long* launches, cudaEvent_t t0, cudaEvent_t t1) {
+  return cholqr_fused_batch(s, 1, &Y, &Q, rows, n, passes, shifted, work, err_word, floored,
+                            flops_out, seed, launches, t0, t1);
 }
 
 }  // namespace ctm

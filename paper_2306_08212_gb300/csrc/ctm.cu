@@ -78,6 +78,8 @@ struct ctm_ctx {
   };
   CacheEntry cache[64];  // 0..47 split isometries, 48..55 standard, 56..63 reduced-env
   int* floored = nullptr;  // CholeskyQR pivots floored (device counter)
+  double* cq_flops = nullptr;  // FP64 flops the CholeskyQR launches executed (device)
+  double cq_flops_base = 0.0;  // its value when the profile counters were cleared
   // CUDA graphs of steady-state moves (mixed precision, reduced-sequential)
   struct GraphEvent {
     int cls;
@@ -493,6 +495,30 @@ Tmp left_svd(ctm_ctx* c, const double* M, int rows, int cols, int k, int slot = 
   return U;
 }
 
+// Under CTM_TRACE (outside captures): the orthogonality error max |G' - I| that
+// each pass of a fused CholeskyQR launch started from.
+void trace_cholqr(ctm_ctx* c, const double* work, int rows, int n, int nprob, int passes) {
+  if (!trace_on() || c->capturing) return;
+  double e[16 * kCholqrMaxProb];
+  if (cholqr_read_emax(c->stream, work, rows, n, nprob, e) != 0) return;
+  std::fprintf(stderr, "[ctm] cholqr %dx%d x%d passes=%d max|G'-I|/||G'-I||_F:", rows, n, nprob,
+               passes);
+  for (int q = 0; q < nprob; ++q) {
+    std::fprintf(stderr, " [");
+    for (int p = 0; p < passes; ++p)
+      std::fprintf(stderr, p ? " %.1e/%.1e" : "%.1e/%.1e", e[16 * q + p],
+                   std::sqrt(e[16 * q + 8 + p]));
+    std::fprintf(stderr, "]");
+  }
+  std::fprintf(stderr, "\n");
+  double ph[8];
+  if (cholqr_read_stamps(c->stream, ph) == 0)
+    std::fprintf(stderr,
+                 "[ctm] cholqr phases ms: gram %.3f reduce %.3f diag %.3f panel %.3f trailing %.3f "
+                 "subst %.3f\n",
+                 ph[1], ph[2], ph[3], ph[4], ph[5], ph[6]);
+}
+
 // Root-mean-square sine of the principal angles between the spans of the
 // leading k columns of Uold and Unew (row-major rows x ld, orthonormal columns):
 // ||Unew_k - Uold_k (Uold_k^T Unew_k)||_F / sqrt(k).  Synchronises the stream.
@@ -627,15 +653,16 @@ Tmp cholqr(ctm_ctx* c, const double* Y, long long ys_r, long long ys_c, int rows
   Tmp Q(c, {rows, n});
   Tmp W(c, {(int)cholqr_work_doubles(rows, n)});
   {
-    const double flops = passes * (2.0 * rows * n * (double)n + (double)n * n * n / 3.0);
-    // the timing events bracket the kernel on the cooperative stream
-    ProfScope ps(c, 4, flops, true);
+    // the timing events bracket the kernel on the cooperative stream; the kernel
+    // adds the flops of the passes it ran to c->cq_flops
+    ProfScope ps(c, 4, 0.0, true);
     const int rc = cholqr_fused(c->stream, Y, Q.t.p, rows, n, passes, true, W.t.p,
-                                &c->flags->error, c->floored, c->seed, &c->launches, ps.ev0(),
-                                ps.ev1());
+                                &c->flags->error, c->floored, c->cq_flops, c->seed,
+                                &c->launches, ps.ev0(), ps.ev1());
     c->seed += passes;
     if (rc != 0) fail(CTM_ERR_CUDA, "fused CholeskyQR launch failed");
   }
+  trace_cholqr(c, W.t.p, rows, n, 1, passes);
   check_finite(c, Q.t, "cholqr");
   return Q;
 }
@@ -883,15 +910,14 @@ void cholqr_batch(ctm_ctx* c, int nprob, const double* const* Y, Tmp* Q, int row
   }
   Tmp W(c, {(int)cholqr_work_doubles(rows, n, nprob)});
   {
-    const double flops =
-        nprob * passes * (2.0 * rows * n * (double)n + (double)n * n * n / 3.0);
-    ProfScope ps(c, 4, flops, true);
+    ProfScope ps(c, 4, 0.0, true);  // flops: counted by the kernel into c->cq_flops
     const int rc = cholqr_fused_batch(c->stream, nprob, Y, qp, rows, n, passes, true, W.t.p,
-                                      &c->flags->error, c->floored, c->seed, &c->launches,
-                                      ps.ev0(), ps.ev1());
+                                      &c->flags->error, c->floored, c->cq_flops, c->seed,
+                                      &c->launches, ps.ev0(), ps.ev1());
     c->seed += passes;
     if (rc != 0) fail(CTM_ERR_CUDA, "fused CholeskyQR launch failed");
   }
+  trace_cholqr(c, W.t.p, rows, n, nprob, passes);
   for (int q = 0; q < nprob; ++q) check_finite(c, Q[q].t, "cholqr");
 }
 
@@ -1620,6 +1646,12 @@ std::vector<std::vector<double>> spectra_all(ctm_ctx* c) {
       fail(CTM_ERR_CUDA, "Jacobi launch failed");
     dfree(c, colver);
   }
+  if (trace_on() && !c->capturing) {
+    DevFlags h;
+    ck(cudaStreamSynchronize(c->stream), "sync");
+    ck(cudaMemcpy(&h, c->flags, sizeof h, cudaMemcpyDeviceToHost), "d2h");
+    std::fprintf(stderr, "[ctm] spectra 8 x %dx%d sweeps=%d\n", nrows, ncols, h.sweeps);
+  }
   Tmp sig(c, {8, ncols});
   int* perm = (int*)dalloc(c, 4 * ncols + 1);
   for (int i = 0; i < 8; ++i) {
@@ -1917,6 +1949,8 @@ int ctm_init_env(ctm_ctx** out, const double* A, const double* B, int d, int D, 
     c->norm_scratch = owned_alloc(c, kNormScratch);
     c->floored = (int*)owned_alloc(c, 1);  // two ints: floored pivots, scratch counter
     ck(cudaMemsetAsync(c->floored, 0, 2 * sizeof(int), c->stream), "floored");
+    c->cq_flops = owned_alloc(c, 1);
+    ck(cudaMemsetAsync(c->cq_flops, 0, sizeof(double), c->stream), "cq_flops");
     if (precision != CTM_FP64) {
       c->tc = tc_create();
       if (!c->tc) fail(CTM_ERR_UNSUPPORTED, "tensor-core GEMM unavailable");
@@ -2371,6 +2405,8 @@ int ctm_profile_enable(ctm_ctx* c, int on) {
       pc.count = 0;
       pc.ms = pc.flops = 0.0;
     }
+    ck(cudaMemcpy(&c->cq_flops_base, c->cq_flops, sizeof(double), cudaMemcpyDeviceToHost),
+       "cq_flops");
     const bool serial = (on & CTM_PROFILE_SERIAL) != 0;
     if ((on & kProfMaskAll) != c->prof_mask || serial != c->prof_serial)
       drop_graphs(c);  // re-capture with the new event set
@@ -2386,6 +2422,11 @@ int ctm_profile_read(ctm_ctx* c, int cls, long long* launches, double* ms, doubl
     *launches = c->prof[cls].count;
     *ms = c->prof[cls].ms;
     *flops = c->prof[cls].flops;
+    if (cls == 4 && ((c->prof_mask >> 4) & 1)) {  // every CholeskyQR launch is timed then
+      double now = 0.0;
+      ck(cudaMemcpy(&now, c->cq_flops, sizeof(double), cudaMemcpyDeviceToHost), "cq_flops");
+      *flops = now - c->cq_flops_base;
+    }
   });
 }
 

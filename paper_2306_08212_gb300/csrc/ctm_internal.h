@@ -127,13 +127,28 @@ constexpr int kCholqrMaxProb = 4;
 size_t cholqr_work_doubles(int rows, int n, int nprob = 1);
 // nprob (<= kCholqrMaxProb) independent problems of the same shape in one launch:
 // they share the barriers and the latency-bound Cholesky steps.
+// `passes` is the most a problem runs: a problem stops after an unshifted pass
+// whose input was already well conditioned.  When flops_out is given, the
+// launch adds the FP64 flops of the passes it ran to it (2 rows n^2 for the Gram
+// and the substitution, n^3 / 3 for a Cholesky; rows n^2 for a pass that only
+// rescales an orthonormal input).
 int cholqr_fused_batch(cudaStream_t s, int nprob, const double* const* Y, double* const* Q,
                        int rows, int n, int passes, bool shifted, double* work, int* err_word,
-                       int* floored, unsigned long long seed, long long* launches,
-                       cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);
+                       int* floored, double* flops_out, unsigned long long seed,
+                       long long* launches, cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);
 int cholqr_fused(cudaStream_t s, const double* Y, double* Q, int rows, int n, int passes,
-                 bool shifted, double* work, int* err_word, int* floored, unsigned long long seed,
-                 long long* launches, cudaEvent_t t0 = nullptr, cudaEvent_t t1 = nullptr);
+                 bool shifted, double* work, int* err_word, int* floored, double* flops_out,
+                 unsigned long long seed, long long* launches, cudaEvent_t t0 = nullptr,
+                 cudaEvent_t t1 = nullptr);
+// Diagnostics: after a launch on `work` (synchronises s), out[q * 16 + pass] =
+// max |G' - I| and out[q * 16 + 8 + pass] = ||G' - I||_F^2 of problem q's scaled
+// Gram in each pass it ran (zero for passes it skipped).
+int cholqr_read_emax(cudaStream_t s, const double* work, int rows, int n, int nprob, double* out);
+// Diagnostics under CTM_TRACE=3: summed ms of the last launch's phases, by tag
+// (1 Gram, 2 reduction, 3 diagonal blocks, 4 panels, 5 trailing updates,
+// 6 substitution).
+unsigned long long* cq_stamps_buffer();
+int cholqr_read_stamps(cudaStream_t s, double* ms_by_tag);
 constexpr double kValuesOnlyTol = 1e-10;
 
 // Column norms of X (nrows x ncols col-major) into sig[ncols]; perm[r] = index of

@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdint>
+#include <cstdio>
 #include <cstdlib>
 #include <map>
 #include <mutex>
@@ -587,6 +588,17 @@ TcChoice rule_of_thumb(long long M, long long N, int nk) {
   return c;
 }
 
+// CTM_TRACE=2 prints every contraction's shape and the device times of its two
+// packs and its GEMM (synchronising after each).
+bool trace_tc() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = std::getenv("CTM_TRACE");
+    on = (e && *e == '2') ? 1 : 0;
+  }
+  return on == 1;
+}
+
 bool capturing(cudaStream_t s) {
   cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
   return cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive;
@@ -615,9 +627,16 @@ int tc_contract(TcGemm* t, cudaStream_t s, int precision, long long M, long long
     if (pa) cudaFreeAsync(pa, s);
     return -2;
   }
+  const bool trace = trace_tc() && !capturing(s);
+  cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (trace)
+    for (auto& ev : tev) cudaEventCreate(&ev);
+  if (trace) cudaEventRecord(tev[0], s);
   cudaError_t e = tf32 ? pack<true>(s, pa, A, Am, Ak, M, K, Kp) : pack<false>(s, pa, A, Am, Ak, M, K, Kp);
+  if (trace) cudaEventRecord(tev[1], s);
   if (e == cudaSuccess)
     e = tf32 ? pack<true>(s, pb, B, Bn, Bk, N, K, Kp) : pack<false>(s, pb, B, Bn, Bk, N, K, Kp);
+  if (trace) cudaEventRecord(tev[2], s);
   *launches += 2;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -704,6 +723,21 @@ int tc_contract(TcGemm* t, cudaStream_t s, int precision, long long M, long long
     if (ev_begin) record(ev_begin, s);
     e = run(choice);  // the result the caller gets (the last launch on C)
     if (ev_end) record(ev_end, s);
+    if (trace) {
+      cudaEventRecord(tev[3], s);
+      cudaEventSynchronize(tev[3]);
+      float ta = 0.f, tb = 0.f, tg = 0.f;
+      cudaEventElapsedTime(&ta, tev[0], tev[1]);
+      cudaEventElapsedTime(&tb, tev[1], tev[2]);
+      cudaEventElapsedTime(&tg, tev[2], tev[3]);
+      const bool at = Am.n > 0 && Am.stride[Am.n - 1] == 1 && !(Ak.n > 0 && Ak.stride[Ak.n - 1] == 1);
+      const bool bt = Bn.n > 0 && Bn.stride[Bn.n - 1] == 1 && !(Bk.n > 0 && Bk.stride[Bk.n - 1] == 1);
+      std::fprintf(stderr,
+                   "[tc] M=%lld N=%lld K=%lld bn=%d splits=%d packA%s %.1f us packB%s %.1f us "
+                   "gemm %.1f us\n",
+                   M, N, K, choice.bn, choice.splits, at ? "(t)" : "", 1e3 * ta, bt ? "(t)" : "",
+                   1e3 * tb, 1e3 * tg);
+    }
     *launches += choice.splits > 1 ? 2 : 1;
     if (e != cudaSuccess) rc = -3;
   }
@@ -714,6 +748,8 @@ int tc_contract(TcGemm* t, cudaStream_t s, int precision, long long M, long long
   if (ws) cudaFreeAsync(ws, s);
   cudaFreeAsync(pa, s);
   cudaFreeAsync(pb, s);
+  if (trace)
+    for (auto& ev : tev) cudaEventDestroy(ev);
   return rc;
 }
 
