@@ -1606,6 +1606,16 @@ std::vector<double> spectrum(ctm_ctx* c, const Ten& C) {
   return out;
 }
 
+// CTM_SPECTRA_PRECONDITION=0 runs the corner Jacobi on the corners themselves.
+bool spectra_precondition_on() {
+  static int on = -1;
+  if (on < 0) {
+    const char* e = std::getenv("CTM_SPECTRA_PRECONDITION");
+    on = (e && *e == '0') ? 0 : 1;
+  }
+  return on == 1;
+}
+
 // Spectra of all 8 corners; one batched Jacobi launch when they share a shape.
 std::vector<std::vector<double>> spectra_all(ctm_ctx* c) {
   std::vector<std::vector<double>> out;
@@ -1624,9 +1634,52 @@ std::vector<std::vector<double>> spectra_all(ctm_ctx* c) {
   const int nrows = cols_side ? n1 : n2, ncols = cols_side ? n2 : n1;
   const long long per = (long long)n1 * n2;
   Tmp X(c, {8, ncols, nrows});
+  // FP32 preconditioning: the same Jacobi run in FP32 (many times the FP64 rate)
+  // yields V_i with C_i V_i nearly orthogonal; V_i orthonormalised in FP64
+  // (CholeskyQR) keeps the singular values of C_i V_i those of C_i, and the FP64
+  // Jacobi on C_i V_i, which decides them, starts close to its end.
+  const bool pre = cols_side && n2 >= 64 && spectra_precondition_on();
+  Tmp Vq[8];
+  int pre_sweeps = 0;
+  if (pre) {
+    Tmp V64(c, {8, n2, n2});
+    {
+      float* X32 = (float*)dalloc(c, 4 * per + 4);       // 8 n1 n2 floats
+      float* V32 = (float*)dalloc(c, 4 * (long long)n2 * n2 + 4);
+      int* colver = (int*)dalloc(c, 4 * (long long)(n2 + 2));
+      const double* cp[8];
+      double* vp[8];
+      for (int i = 0; i < 8; ++i) {
+        cp[i] = c->env[0][i / 2][i % 2].p;
+        vp[i] = V64.t.p + (long long)i * n2 * n2;
+      }
+      ProfScope ps(c, 3, 0.0);
+      if (jacobi_precondition_f32(c->stream, cp, n1, n2, 8, X32, V32, vp, c->flags, 30, 1e-4,
+                                  1e-8, colver, &c->launches) != 0)
+        fail(CTM_ERR_CUDA, "FP32 Jacobi launch failed");
+      dfree(c, X32);
+      dfree(c, V32);
+      dfree(c, colver);
+    }
+    if (trace_on() && !c->capturing) {
+      DevFlags h;
+      ck(cudaStreamSynchronize(c->stream), "sync");
+      ck(cudaMemcpy(&h, c->flags, sizeof h, cudaMemcpyDeviceToHost), "d2h");
+      pre_sweeps = h.sweeps;
+    }
+    for (int i0 = 0; i0 < 8; i0 += kCholqrMaxProb) {
+      const int nb = std::min(kCholqrMaxProb, 8 - i0);
+      const double* wp[kCholqrMaxProb];
+      for (int q = 0; q < nb; ++q) wp[q] = V64.t.p + (long long)(i0 + q) * n2 * n2;
+      cholqr_batch(c, nb, wp, Vq + i0, n2, n2, 3);
+    }
+  }
   for (int i = 0; i < 8; ++i) {
     const Ten& C = c->env[0][i / 2][i % 2];
-    if (cols_side) {
+    if (pre) {  // X_i (column-major n1 x n2) = C_i (row-major) V_i (row-major)
+      gemm64(c, n1, n2, n2, 1.0, C.p, lm1(n1, n2), lm1(n2, 1), Vq[i].t.p, lm1(n2, n2),
+             lm1(n2, 1), 0.0, X.t.p + i * per, lm1(n1, 1), lm1(n2, n1));
+    } else if (cols_side) {
       LegMap m;
       push(m, n2, 1);
       push(m, n1, n2);
@@ -1650,7 +1703,8 @@ std::vector<std::vector<double>> spectra_all(ctm_ctx* c) {
     DevFlags h;
     ck(cudaStreamSynchronize(c->stream), "sync");
     ck(cudaMemcpy(&h, c->flags, sizeof h, cudaMemcpyDeviceToHost), "d2h");
-    std::fprintf(stderr, "[ctm] spectra 8 x %dx%d sweeps=%d\n", nrows, ncols, h.sweeps);
+    std::fprintf(stderr, "[ctm] spectra 8 x %dx%d FP32 sweeps=%d FP64 sweeps=%d\n", nrows,
+                 ncols, pre_sweeps, h.sweeps);
   }
   Tmp sig(c, {8, ncols});
   int* perm = (int*)dalloc(c, 4 * ncols + 1);

@@ -151,6 +151,17 @@ unsigned long long* cq_stamps_buffer();
 int cholqr_read_stamps(cudaStream_t s, double* ms_by_tag);
 constexpr double kValuesOnlyTol = 1e-10;
 
+// Preconditioner of the values-only Jacobi for nprob matrices C[p] (row-major
+// n1 x n2, n2 <= n1): the same dataflow one-sided Jacobi run in FP32 on a copy,
+// with the rotations accumulated into V; Vout[p] (row-major n2 x n2, FP64)
+// receives V, orthonormal to FP32 accuracy.  X and V are FP32 scratch of
+// nprob n1 n2 and nprob n2^2 floats, colver nprob (n2 + 1) ints.  Reaching the
+// sweep cap is not an error.  Returns 0, -1 (arguments) or -3 (launch).
+int jacobi_precondition_f32(cudaStream_t s, const double* const* C, int n1, int n2, int nprob,
+                            float* X, float* V, double* const* Vout, DevFlags* flags,
+                            int max_sweeps, double tol, double tiny_rel, int* colver,
+                            long long* launches);
+
 // Column norms of X (nrows x ncols col-major) into sig[ncols]; perm[r] = index of
 // the r-th largest.  Single-block kernels.
 cudaError_t column_norms_sorted(cudaStream_t s, const double* X, int nrows, int ncols,

@@ -308,10 +308,14 @@ __device__ __forceinline__ void st_release_s32(int* p, int v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// T = float: the same sweeps in FP32 with the rotations also applied to V
+// (ncols x ncols column-major per problem, vstride apart), as a preconditioner
+// for the FP64 run; its sweep cap is not an error (set_noconv = 0).
+template <typename T>
 __global__ void __launch_bounds__(kJacobiThreads)
-jacobi_flow_kernel(double* __restrict__ Xall, int nrows, int ncols, int npad, DevFlags* fl,
+jacobi_flow_kernel(T* __restrict__ Xall, int nrows, int ncols, int npad, DevFlags* fl,
                    int max_sweeps, double tol, int nprob, long long pstride, double tiny_rel,
-                   int* __restrict__ ver) {
+                   int* __restrict__ ver, T* __restrict__ Vall, long long vstride, int set_noconv) {
   const unsigned nblocks = gridDim.x;
   const int npairs = npad / 2;
   const int lane = threadIdx.x % 32;
@@ -323,12 +327,13 @@ jacobi_flow_kernel(double* __restrict__ Xall, int nrows, int ncols, int npad, De
     for (int p = 0; p < nprob; ++p)
       for (long long e = blockIdx.x * (long long)kJacobiThreads + threadIdx.x; e < per;
            e += (long long)gridDim.x * kJacobiThreads)
-        part = fma(Xall[p * pstride + e], Xall[p * pstride + e], part);
+        part = fma((double)Xall[p * pstride + e], (double)Xall[p * pstride + e], part);
     block_sum3<kJacobiThreads>(part, z1, z2);
     if (threadIdx.x == 0 && part > 0.0) atomicAdd(&fl->fro2, part);
     if (!grid_barrier(fl, nblocks)) return;
   }
-  const double tiny = tiny_rel * (*(volatile double*)&fl->fro2);
+  const T tiny = (T)(tiny_rel * (*(volatile double*)&fl->fro2));
+  const T ttol = (T)tol;
   bool failed = false;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     double local_max = 0.0;
@@ -336,7 +341,7 @@ jacobi_flow_kernel(double* __restrict__ Xall, int nrows, int ncols, int npad, De
       const int g = sweep * (npad - 1) + step;  // global step number
       for (int kk = gwarp; kk < npairs * nprob; kk += nwarps) {
         const int k = kk % npairs, p = kk / npairs;
-        double* X = Xall + (long long)p * pstride;
+        T* X = Xall + (long long)p * pstride;
         int* v = ver + (long long)p * npad;
         const int i = rr_col(k, step, npad);
         const int j = rr_col(npad - 1 - k, step, npad);
@@ -351,11 +356,11 @@ jacobi_flow_kernel(double* __restrict__ Xall, int nrows, int ncols, int npad, De
         }
         if (failed) break;
         if (i < ncols && j < ncols) {
-          double* xi = X + (long long)i * nrows;
-          double* xj = X + (long long)j * nrows;
-          double a = 0.0, b = 0.0, gg = 0.0;
+          T* xi = X + (long long)i * nrows;
+          T* xj = X + (long long)j * nrows;
+          T a = 0, b = 0, gg = 0;
           for (int r = lane; r < nrows; r += 32) {
-            const double u = xi[r], w = xj[r];
+            const T u = xi[r], w = xj[r];
             a = fma(u, u, a);
             b = fma(w, w, b);
             gg = fma(u, w, gg);
@@ -365,18 +370,27 @@ jacobi_flow_kernel(double* __restrict__ Xall, int nrows, int ncols, int npad, De
             b += __shfl_xor_sync(0xffffffffu, b, o);
             gg += __shfl_xor_sync(0xffffffffu, gg, o);
           }
-          if (a > 0.0 && b > 0.0) {
-            const double cosang = fabs(gg) / (sqrt(a) * sqrt(b));
-            if (a > tiny && b > tiny) local_max = fmax(local_max, cosang);
-            if (cosang > tol) {
-              const double zeta = (b - a) / (2.0 * gg);
-              const double t = copysign(1.0, zeta) / (fabs(zeta) + hypot(1.0, zeta));
-              const double c = 1.0 / sqrt(1.0 + t * t);
-              const double sn = c * t;
+          if (a > T(0) && b > T(0)) {
+            const T cosang = fabs(gg) / (sqrt(a) * sqrt(b));
+            if (a > tiny && b > tiny) local_max = fmax(local_max, (double)cosang);
+            if (cosang > ttol) {
+              const T zeta = (b - a) / (T(2) * gg);
+              const T t = copysign(T(1), zeta) / (fabs(zeta) + hypot(T(1), zeta));
+              const T c = T(1) / sqrt(T(1) + t * t);
+              const T sn = c * t;
               for (int r = lane; r < nrows; r += 32) {
-                const double u = xi[r], w = xj[r];
+                const T u = xi[r], w = xj[r];
                 xi[r] = c * u - sn * w;
                 xj[r] = sn * u + c * w;
+              }
+              if (Vall) {
+                T* vi = Vall + (long long)p * vstride + (long long)i * ncols;
+                T* vj = Vall + (long long)p * vstride + (long long)j * ncols;
+                for (int r = lane; r < ncols; r += 32) {
+                  const T u = vi[r], w = vj[r];
+                  vi[r] = c * u - sn * w;
+                  vj[r] = sn * u + c * w;
+                }
               }
             }
           }
@@ -413,7 +427,7 @@ jacobi_flow_kernel(double* __restrict__ Xall, int nrows, int ncols, int npad, De
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     fl->sweeps = max_sweeps;
-    atomicExch(&fl->noconv, 1);
+    if (set_noconv) atomicExch(&fl->noconv, 1);
   }
 }
 
@@ -576,10 +590,13 @@ int jacobi_batched(cudaStream_t s, double* X, int nrows, int ncols, int nprob, l
   if (warp_mode && colver) {  // step counters instead of a grid barrier per step
     if (cudaMemsetAsync(colver, 0, sizeof(int) * (size_t)nprob * npad, s) != cudaSuccess)
       return -3;
+    double* Vnone = nullptr;
+    long long vstride = 0;
+    int set_noconv = 1;
     void* fargs[] = {&X, &nrows, &ncols, (void*)&npad, &flags, &max_sweeps, (void*)&tol,
-                     &nprob, &pstride, &tiny_rel, &colver};
-    if (launch_coop_ordered((void*)jacobi_flow_kernel, dim3(grid), dim3(kJacobiThreads), fargs, s,
-                            serialize) != cudaSuccess)
+                     &nprob, &pstride, &tiny_rel, &colver, &Vnone, &vstride, &set_noconv};
+    if (launch_coop_ordered((void*)jacobi_flow_kernel<double>, dim3(grid), dim3(kJacobiThreads),
+                            fargs, s, serialize) != cudaSuccess)
       return -3;
     ++*launches;
     return 0;
@@ -938,6 +955,76 @@ cudaError_t gaussian_fill(cudaStream_t s, double* x, long long n, unsigned long 
   if (blocks < 1) blocks = 1;
   gaussian_kernel<<<(unsigned)blocks, 256, 0, s>>>(x, n, seed);
   return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------
+// FP32 preconditioning of the values-only Jacobi (corner spectra)
+// ---------------------------------------------------------------------------
+// X (column-major n1 x n2, FP32) = C (row-major n1 x n2, FP64), V = identity.
+__global__ void corner_f32_kernel(const double* __restrict__ C, float* __restrict__ X,
+                                  float* __restrict__ V, int n1, int n2) {
+  const long long nn = (long long)n1 * n2, vv = (long long)n2 * n2;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn + vv;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (e < nn) {
+      const long long i = e / n2, j = e % n2;  // reads along C's rows
+      X[j * n1 + i] = (float)C[e];
+    } else {
+      const long long f = e - nn;
+      V[f] = (f / n2 == f % n2) ? 1.f : 0.f;
+    }
+  }
+}
+
+// out (row-major n x n, FP64) = V (column-major n x n, FP32).
+__global__ void v_f64_kernel(const float* __restrict__ V, double* __restrict__ out, int n) {
+  const long long nn = (long long)n * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long i = e / n, j = e % n;
+    out[e] = (double)V[j * n + i];
+  }
+}
+
+int jacobi_precondition_f32(cudaStream_t s, const double* const* C, int n1, int n2, int nprob,
+                            float* X, float* V, double* const* Vout, DevFlags* flags,
+                            int max_sweeps, double tol, double tiny_rel, int* colver,
+                            long long* launches) {
+  if (n2 < 2 || nprob < 1 || n2 > n1) return -1;
+  const long long pstride = (long long)n1 * n2, vstride = (long long)n2 * n2;
+  for (int p = 0; p < nprob; ++p) {
+    long long blocks = (pstride + vstride + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    corner_f32_kernel<<<(unsigned)blocks, 256, 0, s>>>(C[p], X + p * pstride, V + p * vstride, n1,
+                                                      n2);
+    if (cudaGetLastError() != cudaSuccess) return -3;
+    ++*launches;
+  }
+  const int npad = n2 + (n2 & 1);
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const long long want = ((long long)(npad / 2) * nprob + kJacobiThreads / 32 - 1) / (kJacobiThreads / 32);
+  int grid = (int)(want < (long long)nsm ? want : (long long)nsm);
+  if (cudaMemsetAsync(flags, 0, kDevFlagsResetBytes, s) != cudaSuccess ||
+      cudaMemsetAsync(colver, 0, sizeof(int) * (size_t)nprob * npad, s) != cudaSuccess)
+    return -3;
+  int set_noconv = 0;
+  void* fargs[] = {&X, &n1, &n2, (void*)&npad, &flags, &max_sweeps, (void*)&tol, &nprob,
+                   (void*)&pstride, &tiny_rel, &colver, &V, (void*)&vstride, &set_noconv};
+  if (launch_coop_ordered((void*)jacobi_flow_kernel<float>, dim3(grid), dim3(kJacobiThreads),
+                          fargs, s, true) != cudaSuccess)
+    return -3;
+  ++*launches;
+  for (int p = 0; p < nprob; ++p) {
+    long long blocks = (vstride + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    v_f64_kernel<<<(unsigned)blocks, 256, 0, s>>>(V + p * vstride, Vout[p], n2);
+    if (cudaGetLastError() != cudaSuccess) return -3;
+    ++*launches;
+  }
+  return 0;
 }
 
 }  // namespace ctm

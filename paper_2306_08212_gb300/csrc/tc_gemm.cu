@@ -173,11 +173,16 @@ __host__ __device__ constexpr int tc_stages() {
   return BN == 256 ? 4 : 6;
 }
 
+// Dynamic shared memory of a launch whose ring has `nst` stages (at most
+// tc_stages<BN>(); a short K loop takes fewer, so that more CTAs share an SM and
+// one CTA's loads overlap another's epilogue).  The epilogue's staging tiles
+// (4 warps x 32 x 33 floats) reuse the operand stages.
 template <int BN>
-__host__ __device__ constexpr size_t tc_smem_bytes() {
-  return 1024 /*alignment slack*/ + (size_t)tc_stages<BN>() * (kBM + BN) * kStageKBytes +
-         (2 * tc_stages<BN>() + 2) * 8 + (size_t)BN * 8;
+__host__ __device__ constexpr size_t tc_smem_bytes(int nst) {
+  return 1024 /*alignment slack*/ + (size_t)nst * (kBM + BN) * kStageKBytes +
+         (2 * (size_t)nst + 2) * 8 + (size_t)BN * 8;
 }
+static_assert((kBM + 64) * kStageKBytes >= 4 * 32 * 33 * 4, "epilogue staging fits one stage");
 
 // grid (N tiles, M tiles, splits): split z takes k-tiles [z kps, min((z+1) kps, num_k_tiles)).
 // ws == nullptr: the tile is written as FP64 through the output leg maps; else split z
@@ -186,8 +191,7 @@ template <int BN, bool TF32>
 __global__ void __launch_bounds__(128, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                int M, int N, int num_k_tiles, double* __restrict__ C, LegMap Cm, LegMap Cn,
-               int* err, int kps, float* __restrict__ ws) {
-  constexpr int STAGES = tc_stages<BN>();
+               int* err, int kps, float* __restrict__ ws, int n_contig, int STAGES) {
   constexpr uint32_t A_BYTES = kBM * kStageKBytes, B_BYTES = BN * kStageKBytes;
   constexpr int KE = TF32 ? 32 : 64;  // elements of K per stage
   constexpr uint32_t IDESC = make_idesc(kBM, BN, TF32 ? 2u : 1u);
@@ -274,22 +278,44 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
   const int row = warp * 32 + lane;
   const long long m = (long long)m0 + row;
   const long long offm = (m < M) ? tc_map_offset(Cm, m) : 0;
-  if (ok) {
+  if (ok && (n_contig || ws)) {
+    // The output runs along n: each 32 x 32 chunk goes through shared memory (the
+    // operand stages are idle now) so that a warp stores 32 consecutive columns
+    // of one row per instruction.
+    float* stage = reinterpret_cast<float*>(sA) + warp * 32 * 33;
+#pragma unroll 1
+    for (int j0 = 0; j0 < BN; j0 += 32) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)j0, r);
+#pragma unroll
+      for (int i = 0; i < 32; ++i) stage[lane * 33 + i] = __uint_as_float(r[i]);
+      __syncwarp();
+      const long long n = (long long)n0 + j0 + lane;
+      const long long offn = offCn[j0 + lane];
+#pragma unroll 4
+      for (int rr = 0; rr < 32; ++rr) {
+        const long long mr = (long long)m0 + warp * 32 + rr;
+        const long long om = __shfl_sync(0xffffffffu, offm, rr);
+        if (mr < M && n < N) {
+          const float v = stage[rr * 33 + lane];
+          if (ws)
+            ws[((long long)blockIdx.z * M + mr) * N + n] = v;
+          else
+            C[om + offn] = (double)v;
+        }
+      }
+      __syncwarp();
+    }
+  } else if (ok) {
+    // the output runs along m (or neither): a thread stores its own row
 #pragma unroll 1
     for (int j0 = 0; j0 < BN; j0 += 32) {
       uint32_t r[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)j0, r);
       if (m < M) {
-        if (ws) {
-          float* row = ws + ((long long)blockIdx.z * M + m) * N;
 #pragma unroll
-          for (int i = 0; i < 32; ++i)
-            if (n0 + j0 + i < N) row[n0 + j0 + i] = __uint_as_float(r[i]);
-        } else {
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            if (n0 + j0 + i < N) C[offm + offCn[j0 + i]] = (double)__uint_as_float(r[i]);
-          }
+        for (int i = 0; i < 32; ++i) {
+          if (n0 + j0 + i < N) C[offm + offCn[j0 + i]] = (double)__uint_as_float(r[i]);
         }
       }
     }
@@ -334,9 +360,25 @@ __device__ __forceinline__ float round_tf32(float x) {
   return __uint_as_float(y);
 }
 
+// Two consecutive K-positions k, k + 1 (k even; Kp is a multiple of 8, so a
+// pair never crosses a row) stored as one 4-byte (BF16) or 8-byte (TF32) word.
+template <bool TF32>
+__device__ __forceinline__ void pack_store2(void* out, long long o, double v0, double v1) {
+  if constexpr (TF32) {
+    float2 w;
+    w.x = round_tf32((float)v0);
+    w.y = round_tf32((float)v1);
+    *reinterpret_cast<float2*>(static_cast<float*>(out) + o) = w;
+  } else {
+    *reinterpret_cast<__nv_bfloat162*>(static_cast<__nv_bfloat16*>(out) + o) =
+        __halves2bfloat162(__double2bfloat16(v0), __double2bfloat16(v1));
+  }
+}
+
 // Tiled: a block packs 32 rows x 256 K-positions; the leg-map offsets of its
-// rows and K-positions are computed once into shared memory, and writes run
-// along K (coalesced).
+// rows and K-positions are computed once into shared memory; a thread converts
+// two neighbouring K-positions, so a warp reads 64 of them and writes 128 (BF16)
+// or 256 (TF32) contiguous bytes of one row.
 constexpr int kPackRows = 32, kPackK = 256;
 
 template <bool TF32>
@@ -352,24 +394,21 @@ pack_kernel(void* __restrict__ out, const double* __restrict__ in, LegMap Rm, Le
   for (int i = threadIdx.x; i < kPackK; i += blockDim.x)
     offk[i] = (k0 + i < K) ? tc_map_offset(Rk, k0 + i) : 0;
   __syncthreads();
-  for (int e = threadIdx.x; e < kPackRows * kPackK; e += blockDim.x) {
-    const int i = e / kPackK, j = e % kPackK;
+  for (int e = threadIdx.x; e < kPackRows * kPackK / 2; e += blockDim.x) {
+    const int i = e / (kPackK / 2), j = 2 * (e % (kPackK / 2));
     const long long r = r0 + i, k = k0 + j;
     if (r >= R || k >= Kp) continue;
-    const double v = (k < K) ? in[offr[i] + offk[j]] : 0.0;
-    const long long o = r * Kp + k;
-    if constexpr (TF32)
-      static_cast<float*>(out)[o] = round_tf32((float)v);
-    else
-      static_cast<__nv_bfloat16*>(out)[o] = __double2bfloat16(v);
+    const double v0 = (k < K) ? in[offr[i] + offk[j]] : 0.0;
+    const double v1 = (k + 1 < K) ? in[offr[i] + offk[j + 1]] : 0.0;
+    pack_store2<TF32>(out, r * Kp + k, v0, v1);
   }
 }
 
 // Transposing variant for operands whose rows, not their K positions, are
 // contiguous in memory (the innermost row leg has unit stride): a block reads a
-// tile of 64 rows x 32 K-positions along the rows (coalesced), stages it in
-// shared memory and writes it along K.
-constexpr int kPackTR = 64, kPackTK = 32;
+// tile of 64 rows x 64 K-positions along the rows (coalesced), stages it in
+// shared memory and writes it along K, two K-positions per thread.
+constexpr int kPackTR = 64, kPackTK = 64;
 
 template <bool TF32>
 __global__ void __launch_bounds__(256)
@@ -391,16 +430,11 @@ pack_t_kernel(void* __restrict__ out, const double* __restrict__ in, LegMap Rm, 
     tile[kk][rr] = (r < R && k < K) ? in[offr[rr] + offk[kk]] : 0.0;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < kPackTR * kPackTK; e += blockDim.x) {
-    const int kk = e % kPackTK, rr = e / kPackTK;  // K fastest: coalesced writes
+  for (int e = threadIdx.x; e < kPackTR * kPackTK / 2; e += blockDim.x) {
+    const int kk = 2 * (e % (kPackTK / 2)), rr = e / (kPackTK / 2);  // K fastest: coalesced writes
     const long long r = r0 + rr, k = k0 + kk;
     if (r >= R || k >= Kp) continue;
-    const double v = tile[kk][rr];
-    const long long o = r * Kp + k;
-    if constexpr (TF32)
-      static_cast<float*>(out)[o] = round_tf32((float)v);
-    else
-      static_cast<__nv_bfloat16*>(out)[o] = __double2bfloat16(v);
+    pack_store2<TF32>(out, r * Kp + k, tile[kk][rr], tile[kk + 1][rr]);
   }
 }
 
@@ -481,15 +515,32 @@ cudaError_t launch(cudaStream_t s, const CUtensorMap& ma, const CUtensorMap& mb,
   std::call_once(once, [] {
     attr_err = cudaFuncSetAttribute(tc_gemm_kernel<BN, TF32>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)tc_smem_bytes<BN>());
+                                    (int)tc_smem_bytes<BN>(tc_stages<BN>()));
   });
   if (attr_err != cudaSuccess) return attr_err;
   const int kps = (nk + splits - 1) / splits;
   splits = (nk + kps - 1) / kps;  // every split gets at least one k-tile
   dim3 grid((N + BN - 1) / BN, (M + kBM - 1) / kBM, splits);
   if (grid.y > 65535 || grid.z > 65535) return cudaErrorInvalidConfiguration;
-  tc_gemm_kernel<BN, TF32><<<grid, 128, tc_smem_bytes<BN>(), s>>>(ma, mb, M, N, nk, C, Cm, Cn, err,
-                                                                 kps, splits > 1 ? ws : nullptr);
+  // stores run along n when the innermost output leg of n has unit stride
+  const int n_contig = Cn.n > 0 && Cn.stride[Cn.n - 1] == 1 ? 1 : 0;
+  const int nst = kps < tc_stages<BN>() ? kps : tc_stages<BN>();
+  // Shared memory also caps the CTAs an SM holds at the 512 TMEM columns it has
+  // (512 / BN), so that no CTA ever waits in tcgen05.alloc.
+  static int sm_smem = -1;
+  if (sm_smem < 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
+      v = 233472;
+    sm_smem = v;
+  }
+  size_t smem = tc_smem_bytes<BN>(nst);
+  const size_t floor_bytes = (size_t)sm_smem / (512 / BN + 1);
+  if (smem < floor_bytes) smem = floor_bytes;
+  if (smem > tc_smem_bytes<BN>(tc_stages<BN>())) smem = tc_smem_bytes<BN>(tc_stages<BN>());
+  tc_gemm_kernel<BN, TF32><<<grid, 128, smem, s>>>(
+      ma, mb, M, N, nk, C, Cm, Cn, err, kps, splits > 1 ? ws : nullptr, n_contig, nst);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess && splits > 1) {
     long long blocks = ((long long)M * N + 255) / 256;
