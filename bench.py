@@ -404,12 +404,13 @@ def tensor_core_util(breakdown, ms_per_step, peaks):
 # workload, valid only for the kernel source it was taken on: each entry names the source
 # file and the first 16 hex digits of its SHA-256 at capture time; when the file has changed
 # since, the bench reports traffic null.
-# cholqr_f64: 17.5 MB read + written per launch of four 2048 x 256 problems (ncu, D=8 chi=256
-# step); the step's launches carry four problems (v1 and v2 of the boundary factorisations)
-# or two (the reduced networks) in equal numbers, and the traffic is the inputs read once,
-# so it scales with the problem count: 3/4 of the four-problem figure per launch on average.
-TRAFFIC_PER_LAUNCH = {"cholqr_f64": ("paper_2306_08212_gb300/csrc/cholqr.cu", "ad6c55a2a189c45c",
-                                     17.50e6 * 3.0 / 4.0)}
+# cholqr_f64: a launch of four 2048 x 256 problems (16.78 MB of FP64 inputs) read 16.93 MB
+# and wrote 0.29 MB (ncu, D=8 chi=256 step): the inputs once, the outputs still in L2.  The
+# step's 34 launches carry 96 such problems (four or two per launch) and 8 of 256 x 256 (the
+# corner-spectra bases), 406.6 MB of inputs, so the mean launch moves 406.6 / 34 MB x
+# (17.22 / 16.78).
+TRAFFIC_PER_LAUNCH = {"cholqr_f64": ("paper_2306_08212_gb300/csrc/cholqr.cu", "fe352bb7bff5faf5",
+                                     406.6e6 / 34.0 * 17.22 / 16.78)}
 
 
 def measured_traffic(name):
