@@ -321,3 +321,24 @@ def test_reduced_network_is_the_reduced_environment_when_v_l_v_r_keep_their_rang
     # a planted mistake: the sites of the two sublattices exchanged
     Mb = O.reduced_network(O.View(env, 0), "a", {"a": B, "b": A}, chi_env, chip)
     assert np.abs(Mb - Q).max() > 1e-3 * np.abs(Q).max()
+
+
+def test_neel_golden_file_is_the_oracle_run():
+    """tests/golden/neel_d4_chi64_50it.txt comes from the oracle: its first two
+    spectrum changes are reproduced (to the three digits stored)."""
+    vals = {}
+    with open("tests/golden/neel_d4_chi64_50it.txt") as f:
+        for line in f:
+            if not line.startswith("#") and line.strip():
+                key, *rest = line.split()
+                vals[key] = [float(x) for x in rest]
+    A, B = I.neel_sites(4, eps=1e-2, seed=0)
+    env = O.init_env(A, B, 64)
+    spec = O.corner_spectra(env)
+    for it in range(2):
+        for d in O.MOVE_ORDER:
+            O.move(env, d, A, B, 64, 64, "reduced_sequential")
+        new = O.corner_spectra(env)
+        assert abs(O.spectrum_delta(spec, new) - vals["deltas"][it]) <= 2e-3 * vals["deltas"][it]
+        spec = new
+    assert len(vals["deltas"]) == 50 and -0.2501 < vals["energy_mean"][0] < -0.2499
