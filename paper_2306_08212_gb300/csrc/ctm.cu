@@ -462,8 +462,11 @@ Tmp left_svd_impl(ctm_ctx* c, const double* M, int rows, int cols, int k, int pa
                   int slot = -1);
 
 
-// CTM_TRACE=1 prints every factorisation (shape, path, time, Jacobi sweeps of
-// the last launch) to stderr; it synchronises the stream around each call.
+// CTM_TRACE (any non-zero level) prints every factorisation (shape, path, time,
+// Jacobi sweeps of the last launch), the CholeskyQR orthogonality per pass and
+// the sweeps of the corner spectra to stderr, synchronising around each call;
+// level 2 adds every contraction (tc_gemm.cu), level 3 the CholeskyQR phase
+// times (cholqr.cu).
 bool trace_on() {
   static int on = -1;
   if (on < 0) {
