@@ -116,8 +116,11 @@ int ctm_corner_spectrum(ctm_ctx* ctx, int corner, double* s, int* len);
 
 /*
  * All 8 corner spectra at once (same order and scaling as ctm_corner_spectrum;
- * Sec. II), with one batched Jacobi launch when the corners share a shape.  s is a host
- * buffer of 8 * maxlen doubles (row i = corner i); lens[8] receives the counts.
+ * Sec. II), with one batched FP64 Jacobi launch when the corners share a shape.
+ * For corners of 64 or more columns that launch runs on C V, V the rotations of
+ * a batched FP32 Jacobi run on C made orthonormal in FP64 (the values are those
+ * of C; the FP64 run then needs a few sweeps).  s is a host buffer of
+ * 8 * maxlen doubles (row i = corner i); lens[8] receives the counts.
  */
 int ctm_corner_spectra(ctm_ctx* ctx, double* s, int maxlen, int* lens);
 
